@@ -1,0 +1,217 @@
+/*
+ * hasf.h -- C ABI of a GB300 (sm_103a) implementation of the homotopic
+ * alternating sequential filter (HASF) of Mahmoudi & Akil, "Real Time
+ * Topological Image Smoothing On Shared Memory Parallel Machines"
+ * (arXiv:1603.09337).
+ *
+ * What the filter computes (Sec. 2 of the paper).  For a binary image X, a set
+ * of kept points C within X and a set of forbidden points D outside X,
+ *     HASF_n^{C,D} = HF_n^D o HC_n^C o ... o HF_1^D o HC_1^C,
+ * where HC_r^C (homotopic cutting, eq. (i)) and HF_r^D (homotopic filling,
+ * eq. (ii)) are a homotopic opening and closing by the Euclidean disc B_r,
+ * built from exact squared Euclidean distance maps (Sec. 4.1), ball erosion and
+ * dilation, and constrained thinning H / thickening *H that remove or add
+ * simple points only (Sec. 2, Sec. 4.2).  Topology is preserved: the numbers of
+ * n-components of X and nbar-components of its complement never change.
+ *
+ * Fixed readings where the paper is silent (every result is a pure function of
+ * X, C, D, rmax and connectivity):
+ *  - everything outside the image box is background and never changes;
+ *  - H and *H take points by increasing priority level (squared distance,
+ *    computed once on the operator's input), and within a level repeat rounds
+ *    until nothing changes; a round visits the four 2x2 subfields
+ *    (x mod 2, y mod 2) = (0,0), (1,0), (0,1), (1,1) in that order;
+ *  - in eq. (ii), W = eps_r(Z) cup X (the printed eps_n(Y) names an undefined Y).
+ *
+ * Memory.  All image pointers are DEVICE pointers unless an entry point says
+ * otherwise.  Images are row-major uint8, one byte per pixel, rows `pitch`
+ * bytes apart; a non-zero byte is an object pixel.  Outputs are written as
+ * 0/1 bytes.  The caller owns every image buffer; the library reads and writes
+ * them only during the call's device work and keeps no reference afterwards
+ * (for hasf_submit: until hasf_poll reports the job done).  The library owns
+ * its scratch memory, which is taken from the context's byte budget.
+ *
+ * Errors.  Every entry point returns a hasf_status and never aborts the
+ * process.  Argument errors are reported before any device work is issued.
+ * Device-side failures (an iteration cap or a wait deadline) are reported as
+ * HASF_ETIMEOUT by the next synchronising call (hasf_status_of / hasf_poll /
+ * the host-buffer entry points); a CUDA runtime error is HASF_ECUDA.
+ *
+ * Streams.  `stream` arguments are cudaStream_t values passed as void*
+ * (NULL = the legacy default stream).  Calls on one context must be issued to
+ * one stream at a time, or be ordered by the caller: they share the context's
+ * scratch memory.
+ */
+#ifndef HASF_H_
+#define HASF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HASF_OK = 0,
+    HASF_EINVAL = 1,      /* bad argument                                   */
+    HASF_ENOMEM = 2,      /* a device or host allocation failed             */
+    HASF_EBUDGET = 3,     /* the job can never fit the context's budget     */
+    HASF_EPENDING = 4,    /* a submitted job is not finished yet            */
+    HASF_ETIMEOUT = 5,    /* a device iteration cap or wait deadline hit    */
+    HASF_ECUDA = 6,       /* a CUDA runtime call failed                     */
+    HASF_ENOTFOUND = 7,   /* unknown ticket                                 */
+    HASF_ECANCELLED = 8   /* the job was cancelled before it ran            */
+} hasf_status;
+
+/* One image to smooth.  in/out/C/D share `pitch`.  out may equal in.
+ * C == NULL means C is empty; C is used as C cap X (Sec. 2 requires C within X).
+ * D == NULL means D is empty; D is used as D minus X (Sec. 2 requires D in the
+ * complement of X).  width, height in [1, 65536]; pitch >= width;
+ * rmax in [1, 64] is the order n of the filter; connectivity is 8 for
+ * (8,4) adjacency (8-connected object, 4-connected background) or 4 for (4,8). */
+typedef struct hasf_image {
+    const uint8_t *in;
+    uint8_t *out;
+    const uint8_t *C;
+    const uint8_t *D;
+    int32_t width;
+    int32_t height;
+    int32_t pitch;
+    int32_t rmax;
+    int32_t connectivity;
+    int32_t reserved;     /* must be 0 */
+} hasf_image;
+
+typedef struct hasf_ctx hasf_ctx;
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes bounds the
+ * device scratch the context may hold (0 = 20 GiB).  *ctx receives the handle.
+ * Errors: HASF_EINVAL (ctx NULL, bad device), HASF_ENOMEM, HASF_ECUDA. */
+int hasf_create(hasf_ctx **ctx, int device, size_t mem_budget_bytes);
+
+/* Wait for the context's device work, then free everything it owns.
+ * Jobs submitted and not yet finished are cancelled first. */
+int hasf_destroy(hasf_ctx *ctx);
+
+/* Smooth one image, asynchronously on `stream`: HASF_rmax^{C,D}(in) -> out.
+ * Errors: HASF_EINVAL (see hasf_image), HASF_EBUDGET, HASF_ENOMEM,
+ * HASF_ECUDA.  A device-side HASF_ETIMEOUT is reported by hasf_status_of. */
+int hasf_smooth(hasf_ctx *ctx, const hasf_image *img, void *stream);
+
+/* Smooth n independent images in one persistent launch on `stream`.  `imgs`
+ * is a HOST array of n descriptors (each holding device pointers); it may be
+ * reused as soon as the call returns.  Images may differ in size, rmax,
+ * connectivity and constraints.  The result of each image is the same as
+ * hasf_smooth on it alone.  Buffers of different images must not overlap.
+ * Errors as hasf_smooth; n = 0 is a no-op. */
+int hasf_smooth_batch(hasf_ctx *ctx, const hasf_image *imgs, int n, void *stream);
+
+/* Synchronise `stream` and report the device status of the context's last
+ * launches on it: HASF_OK or HASF_ETIMEOUT (and clear it), or HASF_ECUDA. */
+int hasf_status_of(hasf_ctx *ctx, void *stream);
+
+/* Host-buffer form: every pointer in `imgs` is a HOST pointer (ordinary or
+ * pinned memory).  The library stages the images through pinned buffers,
+ * smooths them in batches and copies the results back before returning.
+ * Errors as hasf_smooth_batch, plus HASF_ETIMEOUT. */
+int hasf_smooth_host(hasf_ctx *ctx, const hasf_image *imgs, int n);
+
+/* Serving.  Submit one job (device pointers, which must stay valid until
+ * hasf_poll reports it done).  Jobs are admitted as device slots and budget
+ * free up and run batched with the other jobs in flight (continuous
+ * batching); the result equals hasf_smooth on the same image.
+ * *ticket receives an id.  Errors: HASF_EINVAL, HASF_EBUDGET (the job alone
+ * exceeds the budget). */
+int hasf_submit(hasf_ctx *ctx, const hasf_image *img, uint64_t *ticket);
+
+/* Report a submitted job's state: *done = 1 and *status = its result code
+ * once it has finished (the ticket is then forgotten), else *done = 0.
+ * Errors: HASF_ENOTFOUND (unknown or already reported ticket). */
+int hasf_poll(hasf_ctx *ctx, uint64_t ticket, int *done, int *status);
+
+/* Cancel a submitted job that has not been launched yet: it will be reported
+ * done with status HASF_ECANCELLED.  Errors: HASF_ENOTFOUND (unknown ticket),
+ * HASF_EPENDING (the job is already on the device; it runs to completion). */
+int hasf_cancel(hasf_ctx *ctx, uint64_t ticket);
+
+/* Block until every submitted job has finished. */
+int hasf_drain(hasf_ctx *ctx);
+
+/* Context options (tuning and fault injection), applied to later calls.
+ *   HASF_OPT_FORCE_GANG  (0/1): run every image in gang mode (planes in global
+ *                        memory, several CTAs per image) even if it fits one CTA;
+ *   HASF_OPT_GANG_CTAS   (>= 0): CTAs per gang image, 0 = automatic;
+ *   HASF_OPT_ROUND_CAP   (>= 0): rounds allowed per priority level before the
+ *                        device gives up with HASF_ETIMEOUT, 0 = automatic
+ *                        (pixels + 2, never reached by a correct run);
+ *   HASF_OPT_SERVE_STREAMS (1..16): concurrent batches of the server;
+ *   HASF_OPT_SERVE_BATCH (1..4096): most jobs the server puts in one launch;
+ *   HASF_OPT_STATS       (0/1): count the kernels' work (see hasf_read_stats).
+ * Errors: HASF_EINVAL for an unknown option or value. */
+enum {
+    HASF_OPT_FORCE_GANG = 1,
+    HASF_OPT_GANG_CTAS = 2,
+    HASF_OPT_ROUND_CAP = 3,
+    HASF_OPT_SERVE_STREAMS = 4,
+    HASF_OPT_SERVE_BATCH = 5,
+    HASF_OPT_STATS = 6
+};
+int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
+
+/* Work counters accumulated by launches made while HASF_OPT_STATS was 1,
+ * summed over images: [0] sweep word tests (32-pixel words holding a candidate
+ * of the active subfield), [1] shifted feature words read by level updates,
+ * [2] subfield passes, [3] priority levels that activated points, [4] rounds.
+ * Synchronises the device, copies the first n (1..5) counters to the HOST
+ * array out and resets them.  Errors: HASF_EINVAL, HASF_ECUDA. */
+int hasf_read_stats(hasf_ctx *ctx, uint64_t *out, int n);
+
+/* Static description of a status code. */
+const char *hasf_strerror(int status);
+
+/* ---- Single operators (the same kernels, one step of the filter) --------- */
+
+/* Exact squared Euclidean distance transform (Sec. 4.1, Meijster's two
+ * phases: per-column vertical distance, then per-row lower envelope of
+ * parabolas).  feat: device uint8 image (width x height, row pitch `pitch`
+ * bytes), non-zero = feature point.  If outside_is_feature is non-zero every
+ * point outside the box is a feature too.  d: device int32 array of
+ * width*height values (row-major, no padding) receiving the squared distance,
+ * or -1 where there is no feature at all.  width, height in [1, 32768].
+ * Asynchronous on `stream`; scratch comes from the context. */
+int hasf_edt(hasf_ctx *ctx, const uint8_t *feat, int32_t width, int32_t height,
+             int32_t pitch, int32_t outside_is_feature, int32_t *d, void *stream);
+
+/* One operator of the filter on one image, asynchronously on `stream`:
+ *   op 1: H(Z, W)   -- img->in = Z, img->C = W (NULL = empty); ultimate
+ *                      thinning over priority levels 1..r^2 (points whose
+ *                      priority exceeds r^2 are never removed);
+ *   op 2: *H(Y, V)  -- img->in = Y, img->C = V (required); thickening over
+ *                      levels 1..r^2;
+ *   op 3: HC_r^C    -- img->C as for hasf_smooth;
+ *   op 4: HF_r^D    -- img->D as for hasf_smooth;
+ * with r = img->rmax.  Errors as hasf_smooth. */
+int hasf_operator(hasf_ctx *ctx, int op, const hasf_image *img, void *stream);
+
+/* Evaluate, on the device, the simple-point test the kernels use on all 256
+ * neighbour codes (bit k = neighbour k in the order E, NE, N, NW, W, SW, S,
+ * SE; y grows downward).  out256: HOST array receiving 0/1.  Synchronous. */
+int hasf_simple_table(hasf_ctx *ctx, int32_t connectivity, uint8_t *out256);
+
+/* Priority levels as the fused kernel derives them, for checking it: for
+ * every pixel of the width x height device image `feat` (pitch bytes), the
+ * smallest level l in {sums of two squares <= r^2} such that a point of the
+ * feature set lies within squared distance l, else r^2 + 1.  The feature set
+ * is, by `mode`: 0 = the object pixels of feat (a thickening's priority),
+ * 1 = those plus every point outside the box, 2 = the background pixels of
+ * feat plus every point outside the box (a thinning's priority).
+ * d: device int32, width*height values, row-major.  r in [1, 64]. */
+int hasf_levels(hasf_ctx *ctx, const uint8_t *feat, int32_t width, int32_t height,
+                int32_t pitch, int32_t mode, int32_t r, int32_t *d, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HASF_H_ */

@@ -1,0 +1,820 @@
+// hasf_abi.cu -- host runtime behind the C ABI declared in include/hasf.h.
+//
+// A context owns: a device scratch arena for the synchronous entry points
+// (job descriptors, per-job bit planes), pinned staging for the host-buffer
+// entry point, and the continuous-batching server (a worker thread that
+// admits submitted jobs against the byte budget and launches them in batches
+// on a small pool of streams, so that batches overlap on the device).
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "hasf.h"
+#include "hasf_internal.h"
+
+using namespace hasf;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+int validate(const hasf_image* im) {
+  if (!im || !im->in || !im->out) return HASF_EINVAL;
+  if (im->width < 1 || im->width > 65536 || im->height < 1 || im->height > 65536)
+    return HASF_EINVAL;
+  if (im->pitch < im->width) return HASF_EINVAL;
+  if (im->rmax < 1 || im->rmax > kMaxR) return HASF_EINVAL;
+  if (im->connectivity != 8 && im->connectivity != 4) return HASF_EINVAL;
+  if (im->reserved != 0) return HASF_EINVAL;
+  return HASF_OK;
+}
+
+// Launch plan of a set of jobs: descriptors, resident order, gang CTA map and
+// the byte layout of the scratch they need.
+struct Plan {
+  std::vector<Job> jobs;
+  std::vector<int> order;       // resident jobs, largest work first
+  std::vector<int> gang_jobs;   // gang jobs
+  std::vector<int2> ctamap;     // gang CTAs (job, part)
+  size_t smem = 0;              // dynamic shared memory of the resident launch
+  size_t bytes = 0;             // scratch bytes
+  // offsets inside the scratch block
+  size_t off_jobs = 0, off_order = 0, off_ctamap = 0, off_counter = 0, off_sync = 0,
+         off_status = 0;
+  size_t sync_bytes = 0;
+};
+
+struct Options {
+  int force_gang = 0;
+  int gang_ctas = 0;
+  long long round_cap = 0;
+  int serve_streams = 4;
+  int serve_batch = 512;
+  int stats = 0;
+};
+
+struct Batch {  // one server launch in flight
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  int* h_status = nullptr;  // pinned, one per job
+  std::vector<uint64_t> tickets;
+};
+
+struct Pending {
+  uint64_t ticket;
+  hasf_image img;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct hasf_ctx {
+  int device = 0;
+  size_t budget = 0;
+  int num_sms = 0;
+  size_t max_smem = 0;
+  int gang_max = 0;
+  Options opt;
+
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  int* d_status = nullptr;
+  unsigned long long* d_stats = nullptr;  // STAT_COUNT counters
+
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  void* io = nullptr;
+  size_t io_bytes = 0;
+  cudaStream_t host_stream = nullptr;
+
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Pending> pending;
+  std::vector<Batch> inflight;
+  std::vector<cudaStream_t> free_streams;
+  std::unordered_map<uint64_t, int> finished;
+  std::unordered_set<uint64_t> launched;
+  std::unordered_set<uint64_t> queued;
+  uint64_t next_ticket = 1;
+  size_t inflight_bytes = 0;
+  bool stop = false;
+  std::thread worker;
+  bool worker_running = false;
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HASF_OK;
+  if (e == cudaErrorMemoryAllocation) return HASF_ENOMEM;
+  return HASF_ECUDA;
+}
+
+bool wants_gang(const hasf_ctx* ctx, const hasf_image& im) {
+  if (ctx->opt.force_gang) return true;
+  // keep 1 KB of the per-block limit for the kernel's static shared memory
+  return resident_smem_bytes(im.width, im.height) + 1024 > ctx->max_smem;
+}
+
+int gang_size(const hasf_ctx* ctx, const hasf_image& im) {
+  if (ctx->opt.gang_ctas > 0) return std::min(ctx->opt.gang_ctas, ctx->gang_max);
+  const long long words = (long long)im.height * words_per_row(im.width);
+  long long g = (words + 4095) / 4096;  // about 8 words per thread and pass
+  g = std::max(1LL, std::min(g, (long long)ctx->gang_max));
+  return (int)g;
+}
+
+// Size (base == nullptr) or fill (base != nullptr) the plan of n images.
+// Returns the scratch bytes.
+size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p, char* base,
+                  int* status_ptr) {
+  p.jobs.assign(n, Job{});
+  p.order.clear();
+  p.gang_jobs.clear();
+  p.ctamap.clear();
+  p.smem = 0;
+  size_t off = 0;
+  p.off_jobs = off;
+  off = align_up(off + sizeof(Job) * (size_t)n);
+  p.off_order = off;
+  off = align_up(off + sizeof(int) * (size_t)n);
+  // gang CTAs
+  int gang_ctas = 0;
+  std::vector<char> is_gang(n, 0);
+  for (int i = 0; i < n; ++i) {
+    is_gang[i] = wants_gang(ctx, imgs[i]);
+    if (is_gang[i]) gang_ctas += gang_size(ctx, imgs[i]);
+  }
+  p.off_ctamap = off;
+  off = align_up(off + sizeof(int2) * (size_t)std::max(gang_ctas, 1));
+  p.off_counter = off;
+  off = align_up(off + 16);
+  p.off_sync = off;
+  p.sync_bytes = sizeof(unsigned) * 8 * (size_t)n;
+  off = align_up(off + p.sync_bytes);
+  p.off_status = off;
+  off = align_up(off + sizeof(int) * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const hasf_image& im = imgs[i];
+    Job& j = p.jobs[i];
+    j.in = im.in;
+    j.out = im.out;
+    j.C = im.C;
+    j.D = (op == OP_HASF || op == OP_HF) ? im.D : nullptr;
+    j.w = im.width;
+    j.h = im.height;
+    j.pitch = im.pitch;
+    j.wpr = words_per_row(im.width);
+    j.r_lo = (op == OP_HASF) ? 1 : im.rmax;
+    j.r_hi = im.rmax;
+    j.op = op;
+    j.conn = im.connectivity;
+    j.plane_words = plane_words(im.width, im.height);
+    const long long px = (long long)im.width * im.height;
+    j.cap = ctx->opt.round_cap > 0 ? (int)std::min<long long>(ctx->opt.round_cap, INT_MAX)
+                                   : (int)std::min<long long>(px + 2, INT_MAX);
+    const size_t gwords = (size_t)im.height * j.wpr;
+    j.g0 = base ? (uint32_t*)(base + off) : nullptr;
+    off += align_up(gwords * 4);
+    const bool need_c = (op == OP_THICK) || im.C != nullptr;
+    if (need_c) {
+      j.cp = base ? (uint32_t*)(base + off) : nullptr;
+      off += align_up(gwords * 4);
+    }
+    if (j.D) {
+      j.dp = base ? (uint32_t*)(base + off) : nullptr;
+      off += align_up(gwords * 4);
+    }
+    if (is_gang[i]) {
+      j.gang = gang_size(ctx, im);
+      j.planes = base ? (uint32_t*)(base + off) : nullptr;
+      off += align_up(3ull * (size_t)j.plane_words * 4);
+      j.sync = base ? (unsigned*)(base + p.off_sync) + 8 * i : nullptr;
+      p.gang_jobs.push_back(i);
+    } else {
+      j.gang = 1;
+      p.order.push_back(i);
+      p.smem = std::max(p.smem, resident_smem_bytes(im.width, im.height));
+    }
+    j.status = status_ptr ? status_ptr
+                          : (base ? (int*)(base + p.off_status) + i : nullptr);
+    j.stats = ctx->opt.stats ? ctx->d_stats : nullptr;
+  }
+  // Largest work first (the paper's scheduler bound: a worker never holds
+  // more than its share of the largest tasks).
+  std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
+    const long long wa = (long long)imgs[a].width * imgs[a].height * imgs[a].rmax;
+    const long long wb = (long long)imgs[b].width * imgs[b].height * imgs[b].rmax;
+    return wa > wb;
+  });
+  for (int gi : p.gang_jobs)
+    for (int part = 0; part < p.jobs[gi].gang; ++part) p.ctamap.push_back(make_int2(gi, part));
+  p.bytes = off;
+  return off;
+}
+
+// Upload the plan's descriptors and launch it on `s`.  `base` is the scratch.
+int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s) {
+  const int n = (int)p.jobs.size();
+  std::vector<char> head(p.off_ctamap + sizeof(int2) * std::max<size_t>(p.ctamap.size(), 1), 0);
+  std::memcpy(head.data() + p.off_jobs, p.jobs.data(), sizeof(Job) * n);
+  if (!p.order.empty())
+    std::memcpy(head.data() + p.off_order, p.order.data(), sizeof(int) * p.order.size());
+  if (!p.ctamap.empty())
+    std::memcpy(head.data() + p.off_ctamap, p.ctamap.data(), sizeof(int2) * p.ctamap.size());
+  cudaError_t e = cudaMemcpyAsync(base, head.data(), head.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + p.off_counter, 0, 16, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(base + p.off_sync, 0, p.sync_bytes, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  const Job* d_jobs = (const Job*)(base + p.off_jobs);
+  if (!p.order.empty()) {
+    const int per_sm = std::max(1, resident_ctas_per_sm(ctx->device, p.smem));
+    const int grid = std::min<int>((int)p.order.size(), per_sm * ctx->num_sms);
+    e = launch_resident(d_jobs, (const int*)(base + p.off_order), (int)p.order.size(), grid,
+                        p.smem, (unsigned*)(base + p.off_counter), s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  // Gang jobs: as many as fit co-resident per cooperative launch.
+  size_t at = 0;
+  const int2* d_map = (const int2*)(base + p.off_ctamap);
+  while (at < p.ctamap.size()) {
+    size_t end = at;
+    while (end < p.ctamap.size()) {
+      const int gsz = p.jobs[p.ctamap[end].x].gang;
+      if (end > at && (int)(end - at) + gsz > ctx->gang_max) break;
+      end += gsz;
+    }
+    e = launch_gang(d_jobs, d_map + at, (int)(end - at), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    at = end;
+  }
+  return HASF_OK;
+}
+
+int ensure_arena(hasf_ctx* ctx, size_t bytes, cudaStream_t s) {
+  if (bytes > ctx->budget) return HASF_EBUDGET;
+  if (ctx->arena_bytes >= bytes) return HASF_OK;
+  if (ctx->arena) {
+    cudaStreamSynchronize(s);
+    cudaDeviceSynchronize();
+    cudaFree(ctx->arena);
+    ctx->arena = nullptr;
+    ctx->arena_bytes = 0;
+  }
+  size_t want = std::min(ctx->budget, std::max(bytes, bytes + bytes / 4));
+  cudaError_t e = cudaMalloc(&ctx->arena, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    e = cudaMalloc(&ctx->arena, bytes);
+    want = bytes;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->arena = nullptr;
+    return HASF_ENOMEM;
+  }
+  ctx->arena_bytes = want;
+  return HASF_OK;
+}
+
+// Run n images (device pointers) with operator `op` on stream s, splitting
+// into chunks that fit the budget.
+int run_images(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, cudaStream_t s) {
+  if (n < 0 || (n > 0 && !imgs)) return HASF_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    int v = validate(&imgs[i]);
+    if (v) return v;
+    if (op == OP_THICK && !imgs[i].C) return HASF_EINVAL;
+  }
+  if (n == 0) return HASF_OK;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_status(e);
+  Plan p;
+  int first = 0;
+  while (first < n) {
+    // grow the chunk while it fits the budget
+    int cnt = n - first;
+    size_t need = build_plan(ctx, imgs + first, cnt, op, p, nullptr, nullptr);
+    while (need > ctx->budget && cnt > 1) {
+      cnt = (cnt + 1) / 2;
+      need = build_plan(ctx, imgs + first, cnt, op, p, nullptr, nullptr);
+    }
+    if (need > ctx->budget) return HASF_EBUDGET;
+    int rc = ensure_arena(ctx, need, s);
+    if (rc) return rc;
+    build_plan(ctx, imgs + first, cnt, op, p, (char*)ctx->arena, ctx->d_status);
+    rc = launch_plan(ctx, p, (char*)ctx->arena, s);
+    if (rc) return rc;
+    first += cnt;
+    if (first < n) {
+      // the next chunk reuses the arena: wait for this one
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  return HASF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Server.
+// ---------------------------------------------------------------------------
+
+size_t serve_job_bytes(hasf_ctx* ctx, const hasf_image& im) {
+  Plan p;
+  return build_plan(ctx, &im, 1, OP_HASF, p, nullptr, nullptr);
+}
+
+void retire_finished(hasf_ctx* ctx) {  // ctx->mu held
+  for (size_t i = 0; i < ctx->inflight.size();) {
+    Batch& b = ctx->inflight[i];
+    cudaError_t q = cudaEventQuery(b.done);
+    if (q == cudaErrorNotReady) {
+      ++i;
+      continue;
+    }
+    for (size_t k = 0; k < b.tickets.size(); ++k) {
+      int st = q == cudaSuccess ? b.h_status[k] : HASF_ECUDA;
+      ctx->finished[b.tickets[k]] = st == DEV_TIMEOUT ? HASF_ETIMEOUT : st;
+      ctx->launched.erase(b.tickets[k]);
+    }
+    if (q != cudaSuccess) cudaGetLastError();
+    cudaFreeAsync(b.mem, b.stream);
+    cudaFreeHost(b.h_status);
+    cudaEventDestroy(b.done);
+    ctx->free_streams.push_back(b.stream);
+    ctx->inflight_bytes -= b.bytes;
+    ctx->inflight.erase(ctx->inflight.begin() + i);
+    ctx->cv.notify_all();
+  }
+}
+
+// Admit pending jobs (FIFO) that fit the budget into one batch and launch it.
+bool launch_next(hasf_ctx* ctx) {  // ctx->mu held
+  if (ctx->pending.empty() || ctx->free_streams.empty()) return false;
+  std::vector<hasf_image> imgs;
+  std::vector<uint64_t> tickets;
+  size_t bytes = 0;
+  while (!ctx->pending.empty() && (int)imgs.size() < ctx->opt.serve_batch) {
+    const Pending& pj = ctx->pending.front();
+    if (ctx->inflight_bytes + bytes + pj.bytes + 65536 > ctx->budget) break;
+    imgs.push_back(pj.img);
+    tickets.push_back(pj.ticket);
+    bytes += pj.bytes;
+    ctx->queued.erase(pj.ticket);
+    ctx->pending.pop_front();
+  }
+  if (imgs.empty()) return false;
+  Batch b;
+  b.stream = ctx->free_streams.back();
+  ctx->free_streams.pop_back();
+  b.tickets = tickets;
+  Plan p;
+  const int n = (int)imgs.size();
+  b.bytes = build_plan(ctx, imgs.data(), n, OP_HASF, p, nullptr, nullptr);
+  cudaError_t e = cudaMallocAsync(&b.mem, b.bytes, b.stream);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.h_status, sizeof(int) * n, 0);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+  int rc = cuda_status(e);
+  if (rc == HASF_OK) {
+    build_plan(ctx, imgs.data(), n, OP_HASF, p, (char*)b.mem, nullptr);
+    e = cudaMemsetAsync((char*)b.mem + p.off_status, 0, sizeof(int) * n, b.stream);
+    rc = cuda_status(e);
+    if (rc == HASF_OK) rc = launch_plan(ctx, p, (char*)b.mem, b.stream);
+    if (rc == HASF_OK)
+      rc = cuda_status(cudaMemcpyAsync(b.h_status, (char*)b.mem + p.off_status, sizeof(int) * n,
+                                       cudaMemcpyDeviceToHost, b.stream));
+    if (rc == HASF_OK) rc = cuda_status(cudaEventRecord(b.done, b.stream));
+  }
+  if (rc != HASF_OK) {
+    cudaGetLastError();
+    cudaStreamSynchronize(b.stream);
+    for (uint64_t t : tickets) ctx->finished[t] = rc;
+    if (b.mem) cudaFreeAsync(b.mem, b.stream);
+    if (b.h_status) cudaFreeHost(b.h_status);
+    if (b.done) cudaEventDestroy(b.done);
+    ctx->free_streams.push_back(b.stream);
+    ctx->cv.notify_all();
+    return true;
+  }
+  for (uint64_t t : tickets) ctx->launched.insert(t);
+  ctx->inflight_bytes += b.bytes;
+  ctx->inflight.push_back(b);
+  return true;
+}
+
+void worker_main(hasf_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  while (!ctx->stop || !ctx->inflight.empty()) {
+    retire_finished(ctx);
+    bool launched = false;
+    if (!ctx->stop)
+      while (launch_next(ctx)) launched = true;
+    if (launched) continue;
+    if (ctx->inflight.empty()) {
+      ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->pending.empty(); });
+    } else {
+      // batches on the device: look again shortly
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    }
+  }
+}
+
+int start_server(hasf_ctx* ctx) {  // ctx->mu held
+  if (ctx->worker_running) return HASF_OK;
+  for (int i = 0; i < ctx->opt.serve_streams; ++i) {
+    cudaStream_t st;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+    ctx->free_streams.push_back(st);
+  }
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
+    uint64_t thr = ctx->budget;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  ctx->stop = false;
+  ctx->worker = std::thread(worker_main, ctx);
+  ctx->worker_running = true;
+  return HASF_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI.
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int hasf_create(hasf_ctx** out, int device, size_t mem_budget_bytes) {
+  if (!out) return HASF_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return HASF_ECUDA;
+  }
+  if (device < 0 || device >= ndev) return HASF_EINVAL;
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = upload_level_table();
+  if (e != cudaSuccess) return cuda_status(e);
+  hasf_ctx* c = new (std::nothrow) hasf_ctx();
+  if (!c) return HASF_ENOMEM;
+  c->device = device;
+  c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t)20 << 30;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  c->max_smem = max_resident_smem(device);
+  c->gang_max = std::max(1, max_gang_ctas(device));
+  e = cudaMalloc(&c->d_status, 16);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 16);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, sizeof(unsigned long long) * STAT_COUNT);
+  if (e == cudaSuccess) e = cudaMemset(c->d_stats, 0, sizeof(unsigned long long) * STAT_COUNT);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->host_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    int rc = cuda_status(e);
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return HASF_OK;
+}
+
+int hasf_destroy(hasf_ctx* ctx) {
+  if (!ctx) return HASF_EINVAL;
+  cudaSetDevice(ctx->device);
+  {
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    for (const Pending& pj : ctx->pending) ctx->finished[pj.ticket] = HASF_ECANCELLED;
+    ctx->pending.clear();
+    ctx->queued.clear();
+    ctx->stop = true;
+    ctx->cv.notify_all();
+  }
+  if (ctx->worker_running) ctx->worker.join();
+  for (cudaStream_t st : ctx->free_streams) cudaStreamDestroy(st);
+  cudaDeviceSynchronize();
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->io) cudaFree(ctx->io);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_stats) cudaFree(ctx->d_stats);
+  if (ctx->host_stream) cudaStreamDestroy(ctx->host_stream);
+  delete ctx;
+  return HASF_OK;
+}
+
+int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
+  if (!ctx) return HASF_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  switch (option) {
+    case HASF_OPT_FORCE_GANG:
+      if (value != 0 && value != 1) return HASF_EINVAL;
+      ctx->opt.force_gang = (int)value;
+      return HASF_OK;
+    case HASF_OPT_GANG_CTAS:
+      if (value < 0 || value > 1 << 20) return HASF_EINVAL;
+      ctx->opt.gang_ctas = (int)value;
+      return HASF_OK;
+    case HASF_OPT_ROUND_CAP:
+      if (value < 0) return HASF_EINVAL;
+      ctx->opt.round_cap = value;
+      return HASF_OK;
+    case HASF_OPT_SERVE_STREAMS:
+      if (value < 1 || value > 16 || ctx->worker_running) return HASF_EINVAL;
+      ctx->opt.serve_streams = (int)value;
+      return HASF_OK;
+    case HASF_OPT_SERVE_BATCH:
+      if (value < 1 || value > 4096) return HASF_EINVAL;
+      ctx->opt.serve_batch = (int)value;
+      return HASF_OK;
+    case HASF_OPT_STATS:
+      if (value != 0 && value != 1) return HASF_EINVAL;
+      ctx->opt.stats = (int)value;
+      return HASF_OK;
+    default:
+      return HASF_EINVAL;
+  }
+}
+
+int hasf_smooth(hasf_ctx* ctx, const hasf_image* img, void* stream) {
+  if (!ctx || !img) return HASF_EINVAL;
+  return run_images(ctx, img, 1, OP_HASF, (cudaStream_t)stream);
+}
+
+int hasf_smooth_batch(hasf_ctx* ctx, const hasf_image* imgs, int n, void* stream) {
+  if (!ctx) return HASF_EINVAL;
+  return run_images(ctx, imgs, n, OP_HASF, (cudaStream_t)stream);
+}
+
+int hasf_operator(hasf_ctx* ctx, int op, const hasf_image* img, void* stream) {
+  if (!ctx || !img || op < OP_THIN || op > OP_HF) return HASF_EINVAL;
+  return run_images(ctx, img, 1, op, (cudaStream_t)stream);
+}
+
+int hasf_status_of(hasf_ctx* ctx, void* stream) {
+  if (!ctx) return HASF_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = 0;
+  e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_status(e);
+  return st == DEV_TIMEOUT ? HASF_ETIMEOUT : (st ? HASF_ECUDA : HASF_OK);
+}
+
+int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
+  if (!ctx || n < 0 || (n > 0 && !imgs)) return HASF_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    int v = validate(&imgs[i]);
+    if (v) return v;
+  }
+  if (n == 0) return HASF_OK;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaStream_t s = ctx->host_stream;
+  // Device layout of one image: in, out, [C], [D], each w*h bytes, pitch w.
+  auto img_bytes = [](const hasf_image& im) {
+    const size_t px = (size_t)im.width * im.height;
+    return align_up(px) * (2 + (im.C ? 1 : 0) + (im.D ? 1 : 0));
+  };
+  size_t io_cap = std::max<size_t>(ctx->budget / 4, 64ull << 20);
+  int first = 0;
+  while (first < n) {
+    int cnt = 0;
+    size_t io = 0;
+    while (first + cnt < n && (cnt == 0 || io + img_bytes(imgs[first + cnt]) <= io_cap)) {
+      io += img_bytes(imgs[first + cnt]);
+      ++cnt;
+    }
+    if (ctx->io_bytes < io) {
+      cudaStreamSynchronize(s);
+      if (ctx->io) cudaFree(ctx->io);
+      ctx->io = nullptr;
+      ctx->io_bytes = 0;
+      e = cudaMalloc(&ctx->io, io);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HASF_ENOMEM;
+      }
+      ctx->io_bytes = io;
+    }
+    // Stage through pinned memory unless the caller's buffers are pinned.
+    std::vector<hasf_image> dimgs(cnt);
+    std::vector<size_t> offs(cnt);
+    size_t at = 0;
+    for (int i = 0; i < cnt; ++i) {
+      offs[i] = at;
+      at += img_bytes(imgs[first + i]);
+    }
+    if (ctx->pinned_bytes < io) {
+      if (ctx->pinned) cudaFreeHost(ctx->pinned);
+      ctx->pinned = nullptr;
+      ctx->pinned_bytes = 0;
+      e = cudaHostAlloc(&ctx->pinned, io, 0);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HASF_ENOMEM;
+      }
+      ctx->pinned_bytes = io;
+    }
+    char* pin = (char*)ctx->pinned;
+    char* dev = (char*)ctx->io;
+    for (int i = 0; i < cnt; ++i) {
+      const hasf_image& im = imgs[first + i];
+      const size_t w = im.width, h = im.height, px = w * h, ap = align_up(px);
+      char* d = dev + offs[i];
+      char* hp = pin + offs[i];
+      hasf_image& di = dimgs[i];
+      di = im;
+      di.pitch = im.width;
+      di.in = (const uint8_t*)d;
+      di.out = (uint8_t*)(d + ap);
+      size_t slot = 2;
+      const uint8_t* srcs[2] = {im.C, im.D};
+      const uint8_t** dsts[2] = {&di.C, &di.D};
+      for (int q = 0; q < 2; ++q) {
+        if (!srcs[q]) continue;
+        *dsts[q] = (const uint8_t*)(d + ap * slot);
+        for (size_t y = 0; y < h; ++y)
+          std::memcpy(hp + ap * slot + y * w, srcs[q] + y * (size_t)im.pitch, w);
+        ++slot;
+      }
+      for (size_t y = 0; y < h; ++y) std::memcpy(hp + y * w, im.in + y * (size_t)im.pitch, w);
+      e = cudaMemcpyAsync(d, hp, ap, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && slot > 2)
+        e = cudaMemcpyAsync(d + 2 * ap, hp + 2 * ap, ap * (slot - 2), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    int rc = run_images(ctx, dimgs.data(), cnt, OP_HASF, s);
+    if (rc) return rc;
+    for (int i = 0; i < cnt; ++i) {
+      const size_t px = (size_t)imgs[first + i].width * imgs[first + i].height;
+      const size_t ap = align_up(px);
+      e = cudaMemcpyAsync(pin + offs[i] + ap, dev + offs[i] + ap, px, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    rc = hasf_status_of(ctx, s);
+    if (rc) return rc;
+    for (int i = 0; i < cnt; ++i) {
+      const hasf_image& im = imgs[first + i];
+      const size_t w = im.width, h = im.height, ap = align_up(w * h);
+      for (size_t y = 0; y < h; ++y)
+        std::memcpy(im.out + y * (size_t)im.pitch, pin + offs[i] + ap + y * w, w);
+    }
+    first += cnt;
+  }
+  return HASF_OK;
+}
+
+int hasf_submit(hasf_ctx* ctx, const hasf_image* img, uint64_t* ticket) {
+  if (!ctx || !img || !ticket) return HASF_EINVAL;
+  int v = validate(img);
+  if (v) return v;
+  const size_t bytes = serve_job_bytes(ctx, *img);
+  if (bytes + 65536 > ctx->budget) return HASF_EBUDGET;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  int rc = start_server(ctx);
+  if (rc) return rc;
+  const uint64_t t = ctx->next_ticket++;
+  ctx->pending.push_back(Pending{t, *img, bytes});
+  ctx->queued.insert(t);
+  *ticket = t;
+  ctx->cv.notify_all();
+  return HASF_OK;
+}
+
+int hasf_poll(hasf_ctx* ctx, uint64_t ticket, int* done, int* status) {
+  if (!ctx || !done || !status) return HASF_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->finished.find(ticket);
+  if (it != ctx->finished.end()) {
+    *done = 1;
+    *status = it->second;
+    ctx->finished.erase(it);
+    return HASF_OK;
+  }
+  if (ctx->queued.count(ticket) || ctx->launched.count(ticket)) {
+    *done = 0;
+    *status = HASF_EPENDING;
+    return HASF_OK;
+  }
+  return HASF_ENOTFOUND;
+}
+
+int hasf_cancel(hasf_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return HASF_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->queued.count(ticket)) {
+    for (auto it = ctx->pending.begin(); it != ctx->pending.end(); ++it)
+      if (it->ticket == ticket) {
+        ctx->pending.erase(it);
+        break;
+      }
+    ctx->queued.erase(ticket);
+    ctx->finished[ticket] = HASF_ECANCELLED;
+    return HASF_OK;
+  }
+  if (ctx->launched.count(ticket)) return HASF_EPENDING;
+  return HASF_ENOTFOUND;
+}
+
+int hasf_drain(hasf_ctx* ctx) {
+  if (!ctx) return HASF_EINVAL;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  ctx->cv.wait(lk, [&] { return ctx->pending.empty() && ctx->inflight.empty(); });
+  return HASF_OK;
+}
+
+int hasf_read_stats(hasf_ctx* ctx, uint64_t* out, int n) {
+  if (!ctx || !out || n < 1 || n > STAT_COUNT) return HASF_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  unsigned long long buf[STAT_COUNT] = {0};
+  if (e == cudaSuccess)
+    e = cudaMemcpy(buf, ctx->d_stats, sizeof(buf), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, sizeof(buf));
+  if (e != cudaSuccess) return cuda_status(e);
+  for (int i = 0; i < n; ++i) out[i] = buf[i];
+  return HASF_OK;
+}
+
+const char* hasf_strerror(int status) {
+  switch (status) {
+    case HASF_OK: return "ok";
+    case HASF_EINVAL: return "invalid argument";
+    case HASF_ENOMEM: return "out of memory";
+    case HASF_EBUDGET: return "job exceeds the context's memory budget";
+    case HASF_EPENDING: return "job not finished";
+    case HASF_ETIMEOUT: return "device iteration cap or wait deadline reached";
+    case HASF_ECUDA: return "CUDA runtime error";
+    case HASF_ENOTFOUND: return "unknown ticket";
+    case HASF_ECANCELLED: return "job cancelled";
+    default: return "unknown status";
+  }
+}
+
+int hasf_simple_table(hasf_ctx* ctx, int32_t connectivity, uint8_t* out256) {
+  if (!ctx || !out256 || (connectivity != 8 && connectivity != 4)) return HASF_EINVAL;
+  cudaSetDevice(ctx->device);
+  uint8_t* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 256);
+  if (e == cudaSuccess) e = launch_simple_table(connectivity, d, ctx->host_stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out256, d, 256, cudaMemcpyDeviceToHost, ctx->host_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->host_stream);
+  if (d) cudaFree(d);
+  return cuda_status(e);
+}
+
+int hasf_levels(hasf_ctx* ctx, const uint8_t* feat, int32_t width, int32_t height, int32_t pitch,
+                int32_t mode, int32_t r, int32_t* d, void* stream) {
+  if (!ctx || !feat || !d || width < 1 || height < 1 || width > 65536 || height > 65536 ||
+      pitch < width || r < 1 || r > kMaxR || mode < 0 || mode > 2)
+    return HASF_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t pw = (size_t)plane_words(width, height);
+  int rc = ensure_arena(ctx, 2 * pw * 4, s);
+  if (rc) return rc;
+  uint32_t* f = (uint32_t*)ctx->arena;
+  return cuda_status(launch_levels(feat, width, height, pitch, mode, r, f, f + pw, d, s));
+}
+
+int hasf_edt(hasf_ctx* ctx, const uint8_t* feat, int32_t width, int32_t height, int32_t pitch,
+             int32_t outside_is_feature, int32_t* d, void* stream) {
+  if (!ctx || !feat || !d || width < 1 || height < 1 || width > 32768 || height > 32768 ||
+      pitch < width)
+    return HASF_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t g_bytes = align_up((size_t)width * height * 4);
+  const size_t st_bytes = (size_t)height * 2 * (width + 2) * 4;
+  int rc = ensure_arena(ctx, g_bytes + st_bytes, s);
+  if (rc) return rc;
+  char* base = (char*)ctx->arena;
+  return cuda_status(launch_edt(feat, width, height, pitch, outside_is_feature ? 1 : 0,
+                                (int32_t*)base, (int32_t*)(base + g_bytes), d, s));
+}
+
+}  // extern "C"

@@ -1,0 +1,88 @@
+// hasf_internal.h -- types shared by the host runtime and the kernels of the
+// HASF library (not part of the public C ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hasf {
+
+constexpr int kThreads = 512;      // threads per CTA of the fused kernels
+constexpr int kMaxR = 64;          // largest radius (rmax) supported
+constexpr int kMaxOffsets = 12852; // lattice points v != 0 with |v|^2 <= 64^2
+constexpr int kMaxLevels = 1197;   // sums of two squares in [1, 64^2]
+
+// Operation a job runs.
+enum Op : int {
+  OP_HASF = 0,   // HC_r then HF_r for r = r_lo..r_hi
+  OP_THIN = 1,   // H(Z, W): in = Z, C = W, levels 1..r_hi^2
+  OP_THICK = 2,  // *H(Y, V): in = Y, C = V, levels 1..r_hi^2
+  OP_HC = 3,     // HC_{r_hi}
+  OP_HF = 4,     // HF_{r_hi}
+};
+
+// Work counters a job adds to when Job::stats is set.
+enum StatIndex : int {
+  STAT_WORD_TESTS = 0,  // sweep words holding a candidate of the active subfield
+  STAT_RING_EVALS = 1,  // shifted feature words read by level updates
+  STAT_PASSES = 2,      // subfield passes
+  STAT_LEVELS = 3,      // levels that activated points
+  STAT_ROUNDS = 4,      // rounds
+  STAT_COUNT = 5
+};
+
+// Device status codes written by kernels (a subset of hasf_status).
+enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 5 };
+
+// One image job as the kernels see it.  Planes are bit-packed, 32 pixels per
+// 32-bit word, bit b of word j of row y = pixel (32 j + b, y).
+struct Job {
+  const uint8_t* in;
+  uint8_t* out;
+  const uint8_t* C;
+  const uint8_t* D;
+  uint32_t* g0;      // h * wpr words: snapshot of the operator input
+  uint32_t* cp;      // h * wpr words or null: kept points (C cap X) / W / V
+  uint32_t* dp;      // h * wpr words or null: forbidden points (D minus X)
+  uint32_t* planes;  // gang mode: 3 padded planes (S, F, cand); else null
+  unsigned* sync;    // gang mode: 8 barrier words; else null
+  int* status;       // device status word of the job
+  unsigned long long* stats;  // work counters (see StatIndex) or null
+  int w, h, pitch, wpr;
+  int r_lo, r_hi;
+  int op;
+  int conn;
+  int gang;          // CTAs cooperating on the job (gang mode)
+  int cap;           // rounds allowed per level before DEV_TIMEOUT
+  int plane_words;   // words per padded plane (see plane_words())
+  int pad_;
+};
+
+// Padded plane geometry shared by both modes: rows -1..h, P = wpr + 1 words
+// per row (the extra word and the extra rows are zero: outside the box), one
+// zero word before row -1, rounded up to 4 words.
+__host__ __device__ inline int words_per_row(int w) { return (w + 31) >> 5; }
+__host__ __device__ inline int plane_words(int w, int h) {
+  int P = words_per_row(w) + 1;
+  long long n = (long long)(h + 2) * P + 2;
+  return (int)((n + 3) & ~3LL);
+}
+inline size_t resident_smem_bytes(int w, int h) {
+  return 3ull * (size_t)plane_words(w, h) * 4ull;
+}
+
+// Host launchers (hasf_kernels.cu).
+cudaError_t upload_level_table();
+cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, int grid,
+                            size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
+cudaError_t launch_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);
+int max_gang_ctas(int device);
+size_t max_resident_smem(int device);
+int resident_ctas_per_sm(int device, size_t smem_bytes);
+cudaError_t launch_simple_table(int conn, uint8_t* d_out256, cudaStream_t s);
+cudaError_t launch_levels(const uint8_t* feat, int w, int h, int pitch, int mode, int r,
+                          uint32_t* d_plane_f, uint32_t* d_plane_a, int32_t* d, cudaStream_t s);
+cudaError_t launch_edt(const uint8_t* feat, int w, int h, int pitch, int outside, int32_t* g,
+                       int32_t* stack, int32_t* d, cudaStream_t s);
+
+}  // namespace hasf

@@ -1,0 +1,642 @@
+// hasf_kernels.cu -- fused HASF kernels for sm_103a.
+//
+// One job = one binary image.  Its state lives in three bit-packed planes
+// (32 pixels per 32-bit word):
+//   S     the current set (X, then Y, Z, ... as the operators run);
+//   F     a snapshot of S taken when an operator starts: its distance map
+//         (to the complement of F for a thinning, to F for a thickening) is
+//         the operator's priority, computed once on its input (Sec. 2);
+//   cand  the points currently allowed to change (priority <= current level).
+// Resident mode keeps the three planes of one image in shared memory of one
+// CTA; gang mode keeps them in global memory (L2) for images too large for
+// that, and a gang of co-resident CTAs shares the image, meeting at a
+// global-memory barrier after every sweep.
+//
+// Distances appear only through their sublevel sets.  A point p has priority
+// <= l iff some feature point q lies within squared distance l, i.e. iff q - p
+// is a lattice vector v with |v|^2 <= l.  The kernel walks the levels l that
+// are sums of two squares in increasing order and, at each, ORs the feature
+// plane shifted by the vectors with |v|^2 = l: that adds exactly the points of
+// priority l.  This is the clamped exact EDT of Sec. 4.1 (column distance g,
+// then min over columns of dx^2 + g^2) evaluated as thresholds: values above
+// r^2 are never needed, because every candidate point of every operator call
+// of HC_r / HF_r has priority <= r^2 (the rest lies in the operator's
+// constraint set).  The masks eps_r / delta_r of eqs. (i)-(ii) are therefore
+// implied by the level bound r^2 and need no plane of their own.
+//
+// Simple points (Sec. 2: T = 1 and Tbar = 1) are tested 32 at a time: the
+// eight neighbour planes of a word come from funnel shifts of the 3 x 3 words
+// around it, and the test is the crossing count
+//   sum over the 4-neighbours k in {E, N, W, S} of [x_k = 0 and (x_{k+1} or x_{k+2}) = 1]
+// (cyclic neighbour order E, NE, N, NW, W, SW, S, SE) being exactly 1; for
+// (4,8) adjacency the same count on the complemented neighbours.  The tests
+// check this against the flood-fill definition on all 256 codes.
+//
+// Sweep order: for each level, rounds of the four subfields (x mod 2, y mod 2)
+// = (0,0), (1,0), (0,1), (1,1) until a round changes nothing.  Points of one
+// subfield are never 8-adjacent, so updating a whole subfield at once equals
+// visiting it in raster order.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hasf_internal.h"
+
+namespace hasf {
+
+struct LevelTable {
+  uint16_t value[kMaxLevels];      // sums of two squares, increasing
+  uint16_t start[kMaxLevels + 1];  // vectors of level i: off[start[i] .. start[i+1])
+  uint16_t nlev[kMaxR + 1];        // number of levels <= r^2
+  int8_t off[kMaxOffsets][2];      // (dx, dy)
+};
+
+__constant__ LevelTable c_lv;
+
+// ---------------------------------------------------------------------------
+// Memory / synchronisation policies.
+// ---------------------------------------------------------------------------
+
+struct SmemMode {
+  static __device__ __forceinline__ uint32_t ld(const uint32_t* p) { return *p; }
+  static __device__ __forceinline__ void st(uint32_t* p, uint32_t v) { *p = v; }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ int sync_or(int v) { return __syncthreads_or(v); }
+  __device__ __forceinline__ bool failed() const { return false; }
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Gang barrier: sync[0] = arrivals, sync[1] = generation, sync[4..7] = OR
+// slots indexed by generation mod 4.  Every wait is bounded by a deadline;
+// a CTA that gives up marks the gang failed and leaves the job.
+struct GangMode {
+  unsigned* sync_words;
+  int nctas;
+  int* flag_smem;  // shared int: broadcast of the barrier result
+  int dead;
+  static constexpr unsigned long long kDeadlineNs = 4000000000ull;
+
+  static __device__ __forceinline__ uint32_t ld(const uint32_t* p) { return __ldcg(p); }
+  static __device__ __forceinline__ void st(uint32_t* p, uint32_t v) { __stcg(p, v); }
+
+  __device__ int barrier(int v) {
+    int any = __syncthreads_or(v);
+    if (threadIdx.x == 0) {
+      volatile unsigned* gen = sync_words + 1;
+      unsigned g = *gen;
+      if (any) atomicOr(sync_words + 4 + (g & 3u), 1u);
+      __threadfence();
+      unsigned arrived = atomicAdd(sync_words, 1u);
+      int res = 1;
+      if (arrived == (unsigned)nctas - 1u) {
+        sync_words[0] = 0u;
+        sync_words[4 + ((g + 2u) & 3u)] = 0u;
+        __threadfence();
+        atomicExch(sync_words + 1, g + 1u);
+      } else {
+        unsigned long long t0 = global_ns();
+        unsigned spins = 0;
+        while (*gen == g) {
+          if ((++spins & 255u) == 0u && global_ns() - t0 > kDeadlineNs) { res = 0; break; }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();
+      int out = res ? (int)(*(volatile unsigned*)(sync_words + 4 + (g & 3u)) != 0u) : -1;
+      *flag_smem = out;
+    }
+    __syncthreads();
+    int r = *flag_smem;
+    __syncthreads();
+    if (r < 0) dead = 1;
+    return r > 0;
+  }
+  __device__ __forceinline__ void sync() { barrier(0); }
+  __device__ __forceinline__ int sync_or(int v) { return barrier(v); }
+  __device__ __forceinline__ bool failed() const { return dead != 0; }
+};
+
+// ---------------------------------------------------------------------------
+// Per-job context.
+// ---------------------------------------------------------------------------
+
+template <class Mode>
+struct Ctx {
+  Mode m;
+  uint32_t* S;
+  uint32_t* F;
+  uint32_t* cand;
+  int w, h, wpr, P;
+  uint32_t lastmask;  // valid bits of the last word of each row
+  int gtid, gthreads; // thread index within the job, threads on the job
+  int cap;
+  unsigned n_tests, n_ring;          // per-thread work counters
+  unsigned n_passes, n_levels, n_rounds;
+  __device__ __forceinline__ int idx(int y, int j) const { return (y + 1) * P + j; }
+  __device__ __forceinline__ uint32_t rowmask(int j) const {
+    return j == wpr - 1 ? lastmask : 0xFFFFFFFFu;
+  }
+};
+
+// Simple-point test of the 32 pixels of the word `c` given the 3 x 3 words
+// around it.  Bit b of the result is 1 iff pixel b is simple (removable when
+// in the set, addable when not).
+template <int CONN>
+__device__ __forceinline__ uint32_t simple_bits(uint32_t nw, uint32_t n, uint32_t ne,
+                                                uint32_t wv, uint32_t c, uint32_t e,
+                                                uint32_t sw, uint32_t s, uint32_t se) {
+  uint32_t x0 = __funnelshift_r(c, e, 1);   // E
+  uint32_t x1 = __funnelshift_r(n, ne, 1);  // NE
+  uint32_t x2 = n;                          // N
+  uint32_t x3 = __funnelshift_l(nw, n, 1);  // NW
+  uint32_t x4 = __funnelshift_l(wv, c, 1);  // W
+  uint32_t x5 = __funnelshift_l(sw, s, 1);  // SW
+  uint32_t x6 = s;                          // S
+  uint32_t x7 = __funnelshift_r(s, se, 1);  // SE
+  if (CONN == 4) {
+    x0 = ~x0; x1 = ~x1; x2 = ~x2; x3 = ~x3;
+    x4 = ~x4; x5 = ~x5; x6 = ~x6; x7 = ~x7;
+  }
+  const uint32_t a = ~x0 & (x1 | x2);
+  const uint32_t b = ~x2 & (x3 | x4);
+  const uint32_t cc = ~x4 & (x5 | x6);
+  const uint32_t d = ~x6 & (x7 | x0);
+  const uint32_t odd = a ^ b ^ cc ^ d;
+  const uint32_t two = (a & b) | (cc & d) | ((a | b) & (cc | d));
+  return odd & ~two;
+}
+
+// Word whose bit b is G(32 j + b + dx, y2), where G = F xor inv inside the
+// box and outv outside it.  A thinning reads the complement of its input with
+// the outside as feature (inv = outv = ~0), a thickening its input with an
+// empty outside (inv = outv = 0).
+template <class Mode>
+__device__ __forceinline__ uint32_t fshift(const Ctx<Mode>& k, const uint32_t* Fp, int y2, int j,
+                                           int dx, uint32_t inv, uint32_t outv) {
+  if (y2 < 0 || y2 >= k.h) return outv;
+  const int j0 = j + (dx >> 5);
+  const int sh = dx & 31;
+  const uint32_t* row = Fp + k.idx(y2, 0);
+  uint32_t lo = (j0 >= 0 && j0 < k.wpr) ? (Mode::ld(row + j0) ^ inv) : outv;
+  if (sh == 0) return lo;
+  uint32_t hi = (j0 + 1 >= 0 && j0 + 1 < k.wpr) ? (Mode::ld(row + j0 + 1) ^ inv) : outv;
+  return __funnelshift_r(lo, hi, sh);
+}
+
+// Activate the points of priority level li: cand |= allowed & ring_li(F).
+// Returns (to every thread) whether any point was activated.
+template <class Mode>
+__device__ int level_update(Ctx<Mode>& k, int li, bool thin, const uint32_t* pos,
+                            const uint32_t* neg) {
+  const int o0 = c_lv.start[li], o1 = c_lv.start[li + 1];
+  const uint32_t cm = thin ? 0xFFFFFFFFu : 0u;
+  int act = 0;
+  const int total = k.h * k.wpr;
+  for (int t = k.gtid; t < total; t += k.gthreads) {
+    const int y = t / k.wpr, j = t - y * k.wpr;
+    const int id = k.idx(y, j);
+    const uint32_t s = Mode::ld(k.S + id);
+    const uint32_t cd = Mode::ld(k.cand + id);
+    uint32_t allow = thin ? s : (~s & k.rowmask(j));
+    if (pos) allow &= Mode::ld(pos + t);
+    if (neg) allow &= ~Mode::ld(neg + t);
+    const uint32_t pend = allow & ~cd;
+    if (!pend) continue;
+    uint32_t ring = 0;
+    for (int o = o0; o < o1; ++o) {
+      ring |= fshift(k, k.F, y + c_lv.off[o][1], j, c_lv.off[o][0], cm, cm);
+      ++k.n_ring;
+      if (!(pend & ~ring)) break;
+    }
+    const uint32_t add = pend & ring;
+    if (add) {
+      Mode::st(k.cand + id, cd | add);
+      act = 1;
+    }
+  }
+  return k.m.sync_or(act);
+}
+
+// One subfield pass: change every candidate of the subfield that is simple.
+template <class Mode, int CONN>
+__device__ __forceinline__ int sweep_subfield(Ctx<Mode>& k, int sub, bool thin) {
+  const int sy = sub >> 1;
+  const uint32_t pm = (sub & 1) ? 0xAAAAAAAAu : 0x55555555u;
+  const int nrows = (k.h - sy + 1) >> 1;
+  const int total = nrows * k.wpr;
+  const int P = k.P;
+  uint32_t* S = k.S;
+  int any = 0;
+  for (int t = k.gtid; t < total; t += k.gthreads) {
+    const int i = t / k.wpr, j = t - i * k.wpr;
+    const int id = k.idx(sy + 2 * i, j);
+    const uint32_t cw = Mode::ld(k.cand + id);
+    const uint32_t c = cw & pm;
+    if (!c) continue;
+    ++k.n_tests;
+    const uint32_t ctr = Mode::ld(S + id);
+    const uint32_t sm = simple_bits<CONN>(
+        Mode::ld(S + id - P - 1), Mode::ld(S + id - P), Mode::ld(S + id - P + 1),
+        Mode::ld(S + id - 1), ctr, Mode::ld(S + id + 1),
+        Mode::ld(S + id + P - 1), Mode::ld(S + id + P), Mode::ld(S + id + P + 1));
+    const uint32_t chg = c & sm;
+    if (chg) {
+      Mode::st(S + id, thin ? (ctr & ~chg) : (ctr | chg));
+      Mode::st(k.cand + id, cw & ~chg);
+      any = 1;
+    }
+  }
+  return any;
+}
+
+// Rounds at one level until a round changes nothing.  False on the cap.
+template <class Mode, int CONN>
+__device__ bool run_level(Ctx<Mode>& k, bool thin) {
+  for (int round = 0;; ++round) {
+    if (round >= k.cap) return false;
+    ++k.n_rounds;
+    k.n_passes += 4;
+    int any = 0;
+    for (int sub = 0; sub < 4; ++sub) {
+      any |= sweep_subfield<Mode, CONN>(k, sub, thin);
+      if (sub < 3) k.m.sync();
+    }
+    if (!k.m.sync_or(any)) return !k.m.failed();
+    if (k.m.failed()) return false;
+  }
+}
+
+// One constrained thinning (thin = true, H) or thickening (*H) of S at
+// radius r.  Allowed points: thin -> S minus neg; thick -> (complement of S)
+// cap pos minus neg (pos / neg are unpadded global planes, may be null).
+template <class Mode, int CONN>
+__device__ bool run_operator(Ctx<Mode>& k, int r, bool thin, const uint32_t* pos,
+                             const uint32_t* neg) {
+  const int total = k.h * k.wpr;
+  for (int t = k.gtid; t < total; t += k.gthreads) {
+    const int y = t / k.wpr, j = t - y * k.wpr;
+    const int id = k.idx(y, j);
+    Mode::st(k.F + id, Mode::ld(k.S + id));
+    Mode::st(k.cand + id, 0u);
+  }
+  k.m.sync();
+  const int nlev = c_lv.nlev[r];
+  for (int li = 0; li < nlev; ++li) {
+    const int act = level_update(k, li, thin, pos, neg);
+    if (k.m.failed()) return false;
+    if (!act) continue;
+    ++k.n_levels;
+    if (!run_level<Mode, CONN>(k, thin)) return false;
+  }
+  return true;
+}
+
+template <class Mode>
+__device__ void snapshot(Ctx<Mode>& k, uint32_t* g0) {
+  const int total = k.h * k.wpr;
+  for (int t = k.gtid; t < total; t += k.gthreads) {
+    const int y = t / k.wpr, j = t - y * k.wpr;
+    Mode::st(g0 + t, Mode::ld(k.S + k.idx(y, j)));
+  }
+  k.m.sync();
+}
+
+// Zero the three padded planes, then pack the input (and C, D) into them.
+template <class Mode>
+__device__ void load_job(Ctx<Mode>& k, const Job& jb, uint32_t* planes_base) {
+  const int pw = jb.plane_words;
+  for (int t = k.gtid; t < 3 * pw; t += k.gthreads) Mode::st(planes_base + t, 0u);
+  k.m.sync();
+  const int lane = threadIdx.x & 31;
+  const int gwarp = k.gtid >> 5, nwarps = k.gthreads >> 5;
+  const int total = k.h * k.wpr;
+  const bool cx = jb.op == OP_HASF || jb.op == OP_HC;  // C is taken as C cap X
+  for (int it = gwarp; it < total; it += nwarps) {
+    const int y = it / k.wpr, j = it - y * k.wpr;
+    const int x = (j << 5) + lane;
+    const bool inb = x < k.w;
+    const size_t off = (size_t)y * jb.pitch + x;
+    const uint32_t xs = __ballot_sync(0xFFFFFFFFu, inb && jb.in[off] != 0);
+    uint32_t cs = 0, ds = 0;
+    if (jb.cp) cs = __ballot_sync(0xFFFFFFFFu, inb && jb.C != nullptr && jb.C[off] != 0);
+    if (jb.dp) ds = __ballot_sync(0xFFFFFFFFu, inb && jb.D != nullptr && jb.D[off] != 0);
+    if (lane == 0) {
+      Mode::st(k.S + k.idx(y, j), xs);
+      if (jb.cp) Mode::st(jb.cp + it, cx ? (cs & xs) : cs);
+      if (jb.dp) Mode::st(jb.dp + it, ds & ~xs);
+    }
+  }
+  k.m.sync();
+}
+
+template <class Mode>
+__device__ void store_job(Ctx<Mode>& k, const Job& jb) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = k.gtid >> 5, nwarps = k.gthreads >> 5;
+  const int total = k.h * k.wpr;
+  for (int it = gwarp; it < total; it += nwarps) {
+    const int y = it / k.wpr, j = it - y * k.wpr;
+    const uint32_t s = Mode::ld(k.S + k.idx(y, j));
+    const int x = (j << 5) + lane;
+    if (x < k.w) jb.out[(size_t)y * jb.pitch + x] = (uint8_t)((s >> lane) & 1u);
+  }
+}
+
+// HC_r: Y = H(X, eps_r(X) cup C), then *H(Y, delta_r(Y) cap X) (eq. (i)).
+// HF_r: Z = *H(X, delta_r(X) minus D), then H(Z, eps_r(Z) cup X) (eq. (ii)).
+template <class Mode, int CONN>
+__device__ bool run_hc(Ctx<Mode>& k, const Job& jb, int r) {
+  snapshot(k, jb.g0);
+  if (!run_operator<Mode, CONN>(k, r, true, nullptr, jb.cp)) return false;
+  return run_operator<Mode, CONN>(k, r, false, jb.g0, nullptr);
+}
+template <class Mode, int CONN>
+__device__ bool run_hf(Ctx<Mode>& k, const Job& jb, int r) {
+  snapshot(k, jb.g0);
+  if (!run_operator<Mode, CONN>(k, r, false, nullptr, jb.dp)) return false;
+  return run_operator<Mode, CONN>(k, r, true, nullptr, jb.g0);
+}
+
+template <class Mode, int CONN>
+__device__ void run_job(Ctx<Mode>& k, const Job& jb, uint32_t* planes_base) {
+  load_job(k, jb, planes_base);
+  bool ok = true;
+  switch (jb.op) {
+    case OP_HASF:
+      for (int r = jb.r_lo; ok && r <= jb.r_hi; ++r) {
+        ok = run_hc<Mode, CONN>(k, jb, r);
+        if (ok) ok = run_hf<Mode, CONN>(k, jb, r);
+      }
+      break;
+    case OP_THIN: ok = run_operator<Mode, CONN>(k, jb.r_hi, true, nullptr, jb.cp); break;
+    case OP_THICK: ok = run_operator<Mode, CONN>(k, jb.r_hi, false, jb.cp, nullptr); break;
+    case OP_HC: ok = run_hc<Mode, CONN>(k, jb, jb.r_hi); break;
+    case OP_HF: ok = run_hf<Mode, CONN>(k, jb, jb.r_hi); break;
+    default: ok = false;
+  }
+  if (ok) {
+    store_job(k, jb);
+  } else if (threadIdx.x == 0) {
+    atomicMax(jb.status, (int)DEV_TIMEOUT);
+  }
+  if (jb.stats) {
+    unsigned long long t = k.n_tests, r = k.n_ring;
+    for (int o = 16; o > 0; o >>= 1) {
+      t += __shfl_down_sync(0xFFFFFFFFu, t, o);
+      r += __shfl_down_sync(0xFFFFFFFFu, r, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(jb.stats + STAT_WORD_TESTS, t);
+      atomicAdd(jb.stats + STAT_RING_EVALS, r);
+    }
+    if (k.gtid == 0) {
+      atomicAdd(jb.stats + STAT_PASSES, (unsigned long long)k.n_passes);
+      atomicAdd(jb.stats + STAT_LEVELS, (unsigned long long)k.n_levels);
+      atomicAdd(jb.stats + STAT_ROUNDS, (unsigned long long)k.n_rounds);
+    }
+  }
+}
+
+template <class Mode>
+__device__ __forceinline__ void init_ctx(Ctx<Mode>& k, const Job& jb, uint32_t* base, int gtid,
+                                         int gthreads) {
+  k.w = jb.w;
+  k.h = jb.h;
+  k.wpr = jb.wpr;
+  k.P = jb.wpr + 1;
+  const int rem = jb.w & 31;
+  k.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
+  k.S = base + 1;
+  k.F = base + jb.plane_words + 1;
+  k.cand = base + 2 * jb.plane_words + 1;
+  k.gtid = gtid;
+  k.gthreads = gthreads;
+  k.cap = jb.cap;
+  k.n_tests = k.n_ring = k.n_passes = k.n_levels = k.n_rounds = 0;
+}
+
+// Resident mode: persistent CTAs take jobs from `order` through a counter.
+__global__ void __launch_bounds__(kThreads, 2)
+hasf_resident_kernel(const Job* __restrict__ jobs, const int* __restrict__ order, int njobs,
+                     unsigned* counter) {
+  extern __shared__ uint4 smem4[];
+  uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
+  __shared__ int next;
+  for (;;) {
+    if (threadIdx.x == 0) next = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int slot = next;
+    __syncthreads();
+    if (slot >= njobs) break;
+    const Job& jb = jobs[order[slot]];
+    Ctx<SmemMode> k;
+    init_ctx(k, jb, smem, threadIdx.x, blockDim.x);
+    if (jb.conn == 4) run_job<SmemMode, 4>(k, jb, smem);
+    else run_job<SmemMode, 8>(k, jb, smem);
+    __syncthreads();
+  }
+}
+
+// Gang mode: CTA b works on job ctamap[b].x as part ctamap[b].y of jobs[].gang.
+__global__ void __launch_bounds__(kThreads, 1)
+hasf_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) {
+  __shared__ int flag;
+  const int2 m = ctamap[blockIdx.x];
+  const Job& jb = jobs[m.x];
+  Ctx<GangMode> k;
+  k.m.sync_words = jb.sync;
+  k.m.nctas = jb.gang;
+  k.m.flag_smem = &flag;
+  k.m.dead = 0;
+  init_ctx(k, jb, jb.planes, m.y * blockDim.x + threadIdx.x, jb.gang * blockDim.x);
+  if (jb.conn == 4) run_job<GangMode, 4>(k, jb, jb.planes);
+  else run_job<GangMode, 8>(k, jb, jb.planes);
+}
+
+// All 256 neighbour codes through simple_bits: thread t builds the 3 x 3
+// words whose bit 1 holds the code t's neighbourhood and reads bit 1.
+__global__ void simple_table_kernel(int conn, uint8_t* out) {
+  const int code = threadIdx.x;
+  if (code >= 256) return;
+  // Pixel under test: bit 1 of the centre word.  Neighbour k at (dx, dy).
+  const int dxs[8] = {1, 1, 0, -1, -1, -1, 0, 1};
+  const int dys[8] = {0, -1, -1, -1, 0, 1, 1, 1};
+  uint32_t rows[3] = {0u, 0u, 0u};
+  for (int k = 0; k < 8; ++k)
+    if ((code >> k) & 1) rows[1 + dys[k]] |= 1u << (1 + dxs[k]);
+  const uint32_t r = conn == 4 ? simple_bits<4>(0, rows[0], 0, 0, rows[1], 0, 0, rows[2], 0)
+                               : simple_bits<8>(0, rows[0], 0, 0, rows[1], 0, 0, rows[2], 0);
+  out[code] = (uint8_t)((r >> 1) & 1u);
+}
+
+// Priority levels of every pixel, from the same threshold walk the fused
+// kernel uses (one CTA per row band, packed planes in global memory).
+// Pixels past the width in the last word of a row are outside the box: they
+// are packed as `pad` so that, read through xor inv, they give outv.
+__global__ void levels_pack_kernel(const uint8_t* feat, int w, int h, int pitch, uint32_t* Fp,
+                                   uint32_t pad) {
+  const int wpr = words_per_row(w);
+  const int P = wpr + 1;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int it = gwarp; it < h * wpr; it += nwarps) {
+    const int y = it / wpr, j = it - y * wpr;
+    const int x = (j << 5) + lane;
+    const uint32_t v = __ballot_sync(0xFFFFFFFFu, x < w ? feat[(size_t)y * pitch + x] != 0
+                                                        : ((pad >> lane) & 1u) != 0);
+    if (lane == 0) Fp[1 + (y + 1) * P + j] = v;
+  }
+}
+
+__global__ void levels_walk_kernel(int w, int h, int mode, int r, const uint32_t* Fbase,
+                                   int32_t* d) {
+  Ctx<SmemMode> k;  // geometry only; loads are plain global loads
+  k.w = w;
+  k.h = h;
+  k.wpr = words_per_row(w);
+  k.P = k.wpr + 1;
+  const int rem = w & 31;
+  k.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
+  const uint32_t inv = mode == 2 ? 0xFFFFFFFFu : 0u;
+  const uint32_t outv = mode >= 1 ? 0xFFFFFFFFu : 0u;
+  const uint32_t* F = Fbase + 1;
+  const int nlev = c_lv.nlev[r];
+  const int total = h * k.wpr;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    const int y = t / k.wpr, j = t - y * k.wpr;
+    const uint32_t valid = k.rowmask(j);
+    // Level 0: the feature points themselves.
+    uint32_t done = fshift(k, F, y, j, 0, inv, outv) & valid;
+    int32_t* row = d + (size_t)y * w + (j << 5);
+    for (int b = 0; b < 32; ++b)
+      if ((valid >> b) & 1u) row[b] = ((done >> b) & 1u) ? 0 : r * r + 1;
+    for (int li = 0; li < nlev && done != valid; ++li) {
+      uint32_t ring = 0;
+      for (int o = c_lv.start[li]; o < c_lv.start[li + 1]; ++o)
+        ring |= fshift(k, F, y + c_lv.off[o][1], j, c_lv.off[o][0], inv, outv);
+      uint32_t fresh = ring & valid & ~done;
+      while (fresh) {
+        const int b = __ffs(fresh) - 1;
+        fresh &= fresh - 1u;
+        row[b] = c_lv.value[li];
+      }
+      done |= ring & valid;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+
+cudaError_t upload_level_table() {
+  static LevelTable tab;
+  static bool built = false;
+  if (!built) {
+    // Sort the lattice vectors of the disc of radius kMaxR by squared norm.
+    int n = 0;
+    const int R = kMaxR;
+    static int norms[kMaxOffsets];
+    static int8_t vecs[kMaxOffsets][2];
+    for (int dy = -R; dy <= R; ++dy)
+      for (int dx = -R; dx <= R; ++dx) {
+        const int q = dx * dx + dy * dy;
+        if (q == 0 || q > R * R) continue;
+        norms[n] = q;
+        vecs[n][0] = (int8_t)dx;
+        vecs[n][1] = (int8_t)dy;
+        ++n;
+      }
+    // counting sort by norm (stable)
+    static int count[kMaxR * kMaxR + 2];
+    for (int i = 0; i <= R * R + 1; ++i) count[i] = 0;
+    for (int i = 0; i < n; ++i) ++count[norms[i] + 1];
+    for (int i = 1; i <= R * R + 1; ++i) count[i] += count[i - 1];
+    static int pos[kMaxR * kMaxR + 2];
+    for (int i = 0; i <= R * R + 1; ++i) pos[i] = count[i];
+    for (int i = 0; i < n; ++i) {
+      const int p = pos[norms[i]]++;
+      tab.off[p][0] = vecs[i][0];
+      tab.off[p][1] = vecs[i][1];
+    }
+    int nl = 0;
+    for (int q = 1; q <= R * R; ++q) {
+      if (count[q + 1] == count[q]) continue;
+      tab.value[nl] = (uint16_t)q;
+      tab.start[nl] = (uint16_t)count[q];
+      ++nl;
+    }
+    tab.start[nl] = (uint16_t)n;
+    for (int r = 0; r <= R; ++r) {
+      int c = 0;
+      while (c < nl && tab.value[c] <= r * r) ++c;
+      tab.nlev[r] = (uint16_t)c;
+    }
+    built = (n == kMaxOffsets && nl == kMaxLevels);
+    if (!built) return cudaErrorInvalidValue;
+  }
+  return cudaMemcpyToSymbol(c_lv, &tab, sizeof(tab));
+}
+
+size_t max_resident_smem(int device) {
+  int v = 0;
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  return (size_t)v;
+}
+
+int resident_ctas_per_sm(int device, size_t smem_bytes) {
+  (void)device;
+  int n = 0;
+  cudaFuncSetAttribute(hasf_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem_bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hasf_resident_kernel, kThreads, smem_bytes);
+  return n;
+}
+
+cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, int grid,
+                            size_t smem_bytes, unsigned* d_counter, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(hasf_resident_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  hasf_resident_kernel<<<grid, kThreads, smem_bytes, s>>>(d_jobs, d_order, njobs, d_counter);
+  return cudaGetLastError();
+}
+
+int max_gang_ctas(int device) {
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hasf_gang_kernel, kThreads, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return per_sm * sms;
+}
+
+cudaError_t launch_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s) {
+  void* args[] = {(void*)&d_jobs, (void*)&d_ctamap};
+  return cudaLaunchCooperativeKernel((const void*)hasf_gang_kernel, dim3(nctas), dim3(kThreads),
+                                     args, 0, s);
+}
+
+cudaError_t launch_simple_table(int conn, uint8_t* d_out256, cudaStream_t s) {
+  simple_table_kernel<<<1, 256, 0, s>>>(conn, d_out256);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_levels(const uint8_t* feat, int w, int h, int pitch, int mode, int r,
+                          uint32_t* d_plane_f, uint32_t* d_plane_a, int32_t* d, cudaStream_t s) {
+  const int pw = plane_words(w, h);
+  cudaError_t e = cudaMemsetAsync(d_plane_f, 0, (size_t)pw * 4, s);
+  if (e != cudaSuccess) return e;
+  // mode 1 reads F as is with the outside as feature: pad bits must read 1
+  const uint32_t pad = mode == 1 ? 0xFFFFFFFFu : 0u;
+  (void)d_plane_a;
+  levels_pack_kernel<<<256, 256, 0, s>>>(feat, w, h, pitch, d_plane_f, pad);
+  levels_walk_kernel<<<512, 128, 0, s>>>(w, h, mode, r, d_plane_f, d);
+  return cudaGetLastError();
+}
+
+}  // namespace hasf

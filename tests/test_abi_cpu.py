@@ -1,0 +1,87 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for
+sm_103a, loads, and exports every symbol include/hasf.h declares."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hasf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hasf_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1603_09337_gb300 import build, _lib
+    build.build()
+    return ctypes.CDLL(_lib.LIB_PATH)
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for f in ("hasf_create", "hasf_destroy", "hasf_smooth", "hasf_smooth_batch", "hasf_submit",
+              "hasf_poll", "hasf_cancel", "hasf_strerror", "hasf_edt"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_1603_09337_gb300 import _lib
+    assert sorted(_lib.EXPORTS) == declared_functions()
+
+
+def test_strerror_needs_no_device(lib):
+    lib.hasf_strerror.restype = ctypes.c_char_p
+    assert lib.hasf_strerror(0) == b"ok"
+    assert b"budget" in lib.hasf_strerror(3)
+    assert lib.hasf_strerror(999) == b"unknown status"
+
+
+def test_create_reports_missing_device_without_crashing(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    rc = lib.hasf_create(ctypes.byref(h), 0, ctypes.c_size_t(0))
+    assert rc in (6, 1)   # HASF_ECUDA (no device) or HASF_EINVAL
+    assert not h.value
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.hasf_create(None, 0, ctypes.c_size_t(0)) == 1
+    assert lib.hasf_smooth(None, None, None) == 1
+    assert lib.hasf_destroy(None) == 1
+    assert lib.hasf_poll(None, ctypes.c_uint64(1), None, None) == 1
+
+
+def test_package_import_does_not_load_the_library():
+    import importlib
+    import paper_1603_09337_gb300 as pkg
+    importlib.reload(pkg)
+    assert pkg._lib._lib is None or pkg._lib._lib is not None  # import alone must not raise
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1603_09337_gb300 import _lib
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="not found"):
+            _lib.load(str(tmp_path / "nope.so"))
+    finally:
+        _lib._lib = saved
