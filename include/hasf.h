@@ -210,6 +210,34 @@ int hasf_simple_table(hasf_ctx *ctx, int32_t connectivity, uint8_t *out256);
 int hasf_levels(hasf_ctx *ctx, const uint8_t *feat, int32_t width, int32_t height,
                 int32_t pitch, int32_t mode, int32_t r, int32_t *d, void *stream);
 
+/* ---- Allocation-free form ---------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: latency-critical loops that must not
+ * stall on cudaMalloc (which can synchronise the device), and code inside a
+ * host framework or plug-in whose device memory belongs to that framework's
+ * allocator.  It smooths one image like hasf_smooth, asynchronously on
+ * `stream`, with no context: the kernel's scratch (an input snapshot and the
+ * packed C and D planes) lives in a fixed array inside the library (about
+ * 240 KB, held on every GPU that loads the library until the process exits).
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Limit: height * ceil(width / 32) <= 20480 and the image's three bit planes
+ * must fit one CTA's shared memory (about 1100 rows at 512 columns, 560 rows at
+ * 1024 columns); larger images return HASF_EBUDGET.  Other argument errors
+ * return HASF_EINVAL, as for hasf_smooth.
+ *
+ * `status` is an optional DEVICE int: it is cleared on `stream` and then
+ * receives 0, or HASF_ETIMEOUT if the device iteration cap was hit (NULL: the
+ * status is kept inside the library and not reported).
+ *
+ * The first call on each device (with that device current) does a one-time
+ * set-up: it loads the constant level table and looks up the device address of
+ * the scratch array.  Make that first call before any stream capture.
+ * All calls on one GPU share that GPU's copy of the array, which keeps the last
+ * call's contents: calls that overlap on the GPU (for example on two streams)
+ * race and corrupt each other's results; order them on one stream. */
+int hasf_smooth_noalloc(const hasf_image *img, int *status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTS = (
     "hasf_create", "hasf_destroy", "hasf_smooth", "hasf_smooth_batch", "hasf_status_of",
     "hasf_smooth_host", "hasf_submit", "hasf_poll", "hasf_cancel", "hasf_drain",
     "hasf_set_option", "hasf_strerror", "hasf_edt", "hasf_operator", "hasf_simple_table",
-    "hasf_levels", "hasf_read_stats",
+    "hasf_levels", "hasf_read_stats", "hasf_smooth_noalloc",
 )
 
 
@@ -79,6 +79,7 @@ def _declare(lib):
     lib.hasf_levels.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                 ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.hasf_read_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ci]
+    lib.hasf_smooth_noalloc.argtypes = [img_p, vp, vp]
     for name in EXPORTS:
         if name != "hasf_strerror":
             getattr(lib, name).restype = ci

@@ -37,8 +37,10 @@
 // subfield are never 8-adjacent, so updating a whole subfield at once equals
 // visiting it in raster order.
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
+#include "hasf.h"
 #include "hasf_internal.h"
 
 namespace hasf {
@@ -640,3 +642,112 @@ cudaError_t launch_levels(const uint8_t* feat, int w, int h, int pitch, int mode
 }
 
 }  // namespace hasf
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.
+//
+// Some callers cannot call cudaMalloc: latency-critical loops that must not
+// stall on an allocation (cudaMalloc may synchronise the device), and code
+// running inside a host framework or plug-in whose device memory is owned by
+// that framework's allocator and budget.  hasf_smooth_noalloc serves them: it
+// runs one image through the same fused kernel as hasf_smooth, in resident
+// mode (one CTA, bit planes in shared memory), and keeps the kernel's global
+// scratch -- the operator-input snapshot and the packed C and D planes -- in
+// the file-scope array below instead of memory from a context.  The array is
+// part of the library image: every GPU that loads the library holds it
+// (about 240 KB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace hasf {
+
+constexpr int kStaticPlaneWords = 20480;  // h * ceil(w / 32) words per plane, at most
+constexpr int kStaticWords = 3 * kStaticPlaneWords + 64;  // g0, cp, dp, status
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kStaticWords];
+
+__global__ void __launch_bounds__(kThreads, 2) hasf_single_kernel(Job jb) {
+  extern __shared__ uint4 smem4[];
+  uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
+  Ctx<SmemMode> k;
+  init_ctx(k, jb, smem, threadIdx.x, blockDim.x);
+  if (jb.conn == 4) run_job<SmemMode, 4>(k, jb, smem);
+  else run_job<SmemMode, 8>(k, jb, smem);
+}
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[kMaxDevices] = {};  // device address of the array, per device
+size_t g_noalloc_smem[kMaxDevices] = {};    // opt-in shared memory per block, per device
+}  // namespace
+
+}  // namespace hasf
+
+extern "C" int hasf_smooth_noalloc(const hasf_image* img, int* status, void* stream) {
+  using namespace hasf;
+  if (!img || !img->in || !img->out) return HASF_EINVAL;
+  const int w = img->width, h = img->height;
+  if (w < 1 || w > 65536 || h < 1 || h > 65536 || img->pitch < w || img->rmax < 1 ||
+      img->rmax > kMaxR || (img->connectivity != 8 && img->connectivity != 4) ||
+      img->reserved != 0)
+    return HASF_EINVAL;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HASF_ECUDA;
+  uint32_t* base = nullptr;
+  size_t smem_limit = 0;
+  {
+    // Set-up, once per device, with that device current: the level table and
+    // the device address of the scratch array (its name is only a host-side
+    // stand-in in host code).
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      e = upload_level_table();
+      if (e != cudaSuccess) return HASF_ECUDA;
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) return HASF_ECUDA;
+      int v = 0;
+      e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (e != cudaSuccess) return HASF_ECUDA;
+      e = cudaFuncSetAttribute(hasf_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               v - 1024);
+      if (e != cudaSuccess) return HASF_ECUDA;
+      g_noalloc_smem[dev] = (size_t)v - 1024;
+      g_noalloc_ptr[dev] = (uint32_t*)p;
+    }
+    base = g_noalloc_ptr[dev];
+    smem_limit = g_noalloc_smem[dev];
+  }
+  const long long words = (long long)h * words_per_row(w);
+  const size_t smem = resident_smem_bytes(w, h);
+  if (words > kStaticPlaneWords || smem > smem_limit) return HASF_EBUDGET;
+
+  Job jb{};
+  jb.in = img->in;
+  jb.out = img->out;
+  jb.C = img->C;
+  jb.D = img->D;
+  jb.g0 = base;
+  jb.cp = img->C ? base + kStaticPlaneWords : nullptr;
+  jb.dp = img->D ? base + 2 * kStaticPlaneWords : nullptr;
+  jb.status = status ? status : (int*)(base + 3 * kStaticPlaneWords);
+  jb.w = w;
+  jb.h = h;
+  jb.pitch = img->pitch;
+  jb.wpr = words_per_row(w);
+  jb.r_lo = 1;
+  jb.r_hi = img->rmax;
+  jb.op = OP_HASF;
+  jb.conn = img->connectivity;
+  jb.gang = 1;
+  jb.cap = (int)(words * 32 + 2 < 0x7FFFFFFF ? words * 32 + 2 : 0x7FFFFFFF);
+  jb.plane_words = plane_words(w, h);
+  cudaStream_t s = (cudaStream_t)stream;
+  // The status word must start at zero; the planes are fully written by the
+  // kernel before they are read.
+  e = cudaMemsetAsync(jb.status, 0, sizeof(int), s);
+  if (e != cudaSuccess) return HASF_ECUDA;
+  hasf_single_kernel<<<1, kThreads, smem, s>>>(jb);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? HASF_OK : HASF_ECUDA;
+}
