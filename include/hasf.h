@@ -147,7 +147,10 @@ int hasf_drain(hasf_ctx *ctx);
  *                        (pixels + 2, never reached by a correct run);
  *   HASF_OPT_SERVE_STREAMS (1..16): concurrent batches of the server;
  *   HASF_OPT_SERVE_BATCH (1..4096): most jobs the server puts in one launch;
- *   HASF_OPT_STATS       (0/1): count the kernels' work (see hasf_read_stats).
+ *   HASF_OPT_STATS       (0/1): count the kernels' work (see hasf_read_stats);
+ *   HASF_OPT_GENERIC_ONLY (0/1): run images up to 512 x 512 on the generic
+ *                        shared-memory kernel instead of the register kernel
+ *                        (the result is the same; for comparisons).
  * Errors: HASF_EINVAL for an unknown option or value. */
 enum {
     HASF_OPT_FORCE_GANG = 1,
@@ -155,7 +158,8 @@ enum {
     HASF_OPT_ROUND_CAP = 3,
     HASF_OPT_SERVE_STREAMS = 4,
     HASF_OPT_SERVE_BATCH = 5,
-    HASF_OPT_STATS = 6
+    HASF_OPT_STATS = 6,
+    HASF_OPT_GENERIC_ONLY = 7
 };
 int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
 

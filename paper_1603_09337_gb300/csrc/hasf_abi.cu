@@ -46,7 +46,9 @@ int validate(const hasf_image* im) {
 // the byte layout of the scratch they need.
 struct Plan {
   std::vector<Job> jobs;
-  std::vector<int> order;       // resident jobs, largest work first
+  std::vector<int> order;       // resident jobs (generic kernel), largest work first
+  std::vector<int> reg_order;   // resident jobs (register kernel), largest work first
+  size_t reg_smem = 0;          // dynamic shared memory of the register launch
   std::vector<int> gang_jobs;   // gang jobs
   std::vector<int2> ctamap;     // gang CTAs (job, part)
   size_t smem = 0;              // dynamic shared memory of the resident launch
@@ -64,6 +66,7 @@ struct Options {
   int serve_streams = 4;
   int serve_batch = 512;
   int stats = 0;
+  int generic_only = 0;
 };
 
 struct Batch {  // one server launch in flight
@@ -145,6 +148,8 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
                   int* status_ptr) {
   p.jobs.assign(n, Job{});
   p.order.clear();
+  p.reg_order.clear();
+  p.reg_smem = 0;
   p.gang_jobs.clear();
   p.ctamap.clear();
   p.smem = 0;
@@ -203,9 +208,13 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
     if (is_gang[i]) {
       j.gang = gang_size(ctx, im);
       j.planes = base ? (uint32_t*)(base + off) : nullptr;
-      off += align_up(3ull * (size_t)j.plane_words * 4);
+      off += align_up(state_bytes(im.width, im.height));
       j.sync = base ? (unsigned*)(base + p.off_sync) + 8 * i : nullptr;
       p.gang_jobs.push_back(i);
+    } else if (!ctx->opt.generic_only && reg_kernel_ok(im.width, im.height)) {
+      j.gang = 1;
+      p.reg_order.push_back(i);
+      p.reg_smem = std::max(p.reg_smem, reg_kernel_smem(im.width, im.height));
     } else {
       j.gang = 1;
       p.order.push_back(i);
@@ -217,11 +226,13 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
   }
   // Largest work first (the paper's scheduler bound: a worker never holds
   // more than its share of the largest tasks).
-  std::stable_sort(p.order.begin(), p.order.end(), [&](int a, int b) {
+  auto by_work = [&](int a, int b) {
     const long long wa = (long long)imgs[a].width * imgs[a].height * imgs[a].rmax;
     const long long wb = (long long)imgs[b].width * imgs[b].height * imgs[b].rmax;
     return wa > wb;
-  });
+  };
+  std::stable_sort(p.order.begin(), p.order.end(), by_work);
+  std::stable_sort(p.reg_order.begin(), p.reg_order.end(), by_work);
   for (int gi : p.gang_jobs)
     for (int part = 0; part < p.jobs[gi].gang; ++part) p.ctamap.push_back(make_int2(gi, part));
   p.bytes = off;
@@ -235,6 +246,9 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s) {
   std::memcpy(head.data() + p.off_jobs, p.jobs.data(), sizeof(Job) * n);
   if (!p.order.empty())
     std::memcpy(head.data() + p.off_order, p.order.data(), sizeof(int) * p.order.size());
+  if (!p.reg_order.empty())
+    std::memcpy(head.data() + p.off_order + sizeof(int) * p.order.size(), p.reg_order.data(),
+                sizeof(int) * p.reg_order.size());
   if (!p.ctamap.empty())
     std::memcpy(head.data() + p.off_ctamap, p.ctamap.data(), sizeof(int2) * p.ctamap.size());
   cudaError_t e = cudaMemcpyAsync(base, head.data(), head.size(), cudaMemcpyHostToDevice, s);
@@ -242,6 +256,14 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s) {
   if (e == cudaSuccess) e = cudaMemsetAsync(base + p.off_sync, 0, p.sync_bytes, s);
   if (e != cudaSuccess) return cuda_status(e);
   const Job* d_jobs = (const Job*)(base + p.off_jobs);
+  if (!p.reg_order.empty()) {
+    const int per_sm = std::max(1, reg_ctas_per_sm(p.reg_smem));
+    const int grid = std::min<int>((int)p.reg_order.size(), per_sm * ctx->num_sms);
+    e = launch_reg(d_jobs, (const int*)(base + p.off_order) + p.order.size(),
+                   (int)p.reg_order.size(), grid, p.reg_smem,
+                   (unsigned*)(base + p.off_counter) + 1, s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
   if (!p.order.empty()) {
     const int per_sm = std::max(1, resident_ctas_per_sm(ctx->device, p.smem));
     const int grid = std::min<int>((int)p.order.size(), per_sm * ctx->num_sms);
@@ -551,6 +573,10 @@ int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
     case HASF_OPT_STATS:
       if (value != 0 && value != 1) return HASF_EINVAL;
       ctx->opt.stats = (int)value;
+      return HASF_OK;
+    case HASF_OPT_GENERIC_ONLY:
+      if (value != 0 && value != 1) return HASF_EINVAL;
+      ctx->opt.generic_only = (int)value;
       return HASF_OK;
     default:
       return HASF_EINVAL;

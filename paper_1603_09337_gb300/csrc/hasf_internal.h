@@ -58,24 +58,36 @@ struct Job {
   int pad_;
 };
 
-// Padded plane geometry shared by both modes: rows -1..h, P = wpr + 1 words
-// per row (the extra word and the extra rows are zero: outside the box), one
-// zero word before row -1, rounded up to 4 words.
+// Padded plane geometry shared by both modes: rows -1..h, P words per row
+// (P = the first odd number above the words of a row; the extra words and
+// rows are zero: outside the box), one zero word before row -1, rounded up
+// to 4 words.  P odd lets two half-warps on rows 16 apart (or quarter-warps
+// on rows 8 apart ...) hit disjoint shared-memory banks.
 __host__ __device__ inline int words_per_row(int w) { return (w + 31) >> 5; }
+__host__ __device__ inline int row_pitch(int w) {
+  const int wpr = words_per_row(w);
+  return wpr + 1 + (wpr & 1);
+}
 __host__ __device__ inline int plane_words(int w, int h) {
-  int P = words_per_row(w) + 1;
-  long long n = (long long)(h + 2) * P + 2;
+  long long n = (long long)(h + 2) * row_pitch(w) + 2;
   return (int)((n + 3) & ~3LL);
 }
-inline size_t resident_smem_bytes(int w, int h) {
-  return 3ull * (size_t)plane_words(w, h) * 4ull;
+__host__ __device__ inline int dirty_words(int, int) { return 0; }
+inline size_t state_bytes(int w, int h) {
+  return (3ull * (size_t)plane_words(w, h) + (size_t)dirty_words(w, h)) * 4ull;
 }
+inline size_t resident_smem_bytes(int w, int h) { return state_bytes(w, h); }
 
 // Host launchers (hasf_kernels.cu).
 cudaError_t upload_level_table();
 cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, int grid,
                             size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
 cudaError_t launch_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);
+size_t reg_kernel_smem(int w, int h);
+bool reg_kernel_ok(int w, int h);
+int reg_ctas_per_sm(size_t smem_bytes);
+cudaError_t launch_reg(const Job* d_jobs, const int* d_order, int njobs, int grid,
+                       size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
 int max_gang_ctas(int device);
 size_t max_resident_smem(int device);
 int resident_ctas_per_sm(int device, size_t smem_bytes);

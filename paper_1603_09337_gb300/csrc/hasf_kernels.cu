@@ -61,6 +61,7 @@ __constant__ LevelTable c_lv;
 struct SmemMode {
   static __device__ __forceinline__ uint32_t ld(const uint32_t* p) { return *p; }
   static __device__ __forceinline__ void st(uint32_t* p, uint32_t v) { *p = v; }
+  static __device__ __forceinline__ void atomic_or(uint32_t* p, uint32_t v) { atomicOr(p, v); }
   __device__ __forceinline__ void sync() { __syncthreads(); }
   __device__ __forceinline__ int sync_or(int v) { return __syncthreads_or(v); }
   __device__ __forceinline__ bool failed() const { return false; }
@@ -84,6 +85,7 @@ struct GangMode {
 
   static __device__ __forceinline__ uint32_t ld(const uint32_t* p) { return __ldcg(p); }
   static __device__ __forceinline__ void st(uint32_t* p, uint32_t v) { __stcg(p, v); }
+  static __device__ __forceinline__ void atomic_or(uint32_t* p, uint32_t v) { atomicOr(p, v); }
 
   __device__ int barrier(int v) {
     int any = __syncthreads_or(v);
@@ -126,15 +128,34 @@ struct GangMode {
 // Per-job context.
 // ---------------------------------------------------------------------------
 
+// Thread-to-word walk over a set of rows (every row, or every other row).
+// A warp covers 32 consecutive words of one row when rows have more than 32
+// words; otherwise it splits into g = 32 / L groups of L lanes (L = the power
+// of two >= words per row), group k taking the row k * delta (set indices)
+// below group 0.  delta makes the groups' addresses differ by L words modulo
+// 32 (the row pitch is odd, so it has an inverse modulo 32), so that the
+// groups hit disjoint shared-memory banks.  Rows are visited in tuples of g;
+// tuple t is block t / delta, offset t % delta; warps take tuples round robin.
+struct Walk {
+  int delta;   // group stride in row-set indices
+  int block;   // rows per block (g * delta)
+  int b0, m0;  // this warp's first tuple
+  int db, dm;  // tuple advance per step (nwarps tuples)
+};
+
 template <class Mode>
 struct Ctx {
   Mode m;
   uint32_t* S;
   uint32_t* F;
   uint32_t* cand;
-  int w, h, wpr, P;
+  uint32_t* dirty;    // 2 planes of h * dwpr words
+  int w, h, wpr, P, dwpr;
   uint32_t lastmask;  // valid bits of the last word of each row
   int gtid, gthreads; // thread index within the job, threads on the job
+  int wid, nwarps;    // warp index within the job, warps on the job
+  int L, grp, lj, nchunks;
+  Walk walk1, walk2;  // every row / every other row
   int cap;
   unsigned n_tests, n_ring;          // per-thread work counters
   unsigned n_passes, n_levels, n_rounds;
@@ -143,6 +164,24 @@ struct Ctx {
     return j == wpr - 1 ? lastmask : 0xFFFFFFFFu;
   }
 };
+
+__device__ __forceinline__ void walk_init(Walk& wk, int step, int L, int g, int P, int wid,
+                                          int nwarps) {
+  if (g == 1) {
+    wk.delta = 1;
+  } else {
+    int pinv = 1;
+    while (((pinv * P) & 31) != 1) pinv += 2;  // P is odd: an inverse exists
+    int d = (L * pinv) & 31;
+    if (step == 2 && (d & 1) == 0) d >>= 1;
+    wk.delta = d > 0 ? d : 1;
+  }
+  wk.block = g * wk.delta;
+  wk.b0 = wid / wk.delta;
+  wk.m0 = wid % wk.delta;
+  wk.db = nwarps / wk.delta;
+  wk.dm = nwarps % wk.delta;
+}
 
 // Simple-point test of the 32 pixels of the word `c` given the 3 x 3 words
 // around it.  Bit b of the result is 1 iff pixel b is simple (removable when
@@ -190,27 +229,39 @@ __device__ __forceinline__ uint32_t fshift(const Ctx<Mode>& k, const uint32_t* F
 }
 
 // Activate the points of priority level li: cand |= allowed & ring_li(F).
-// Returns (to every thread) whether any point was activated.
+// Returns (to every thread) whether any point was activated.  Each thread
+// walks its own words with no warp collective in the loop, so that lanes
+// drift apart and the irregular ring loops of different words share warp
+// instructions.
 template <class Mode>
 __device__ int level_update(Ctx<Mode>& k, int li, bool thin, const uint32_t* pos,
                             const uint32_t* neg) {
   const int o0 = c_lv.start[li], o1 = c_lv.start[li + 1];
   const uint32_t cm = thin ? 0xFFFFFFFFu : 0u;
   int act = 0;
-  const int total = k.h * k.wpr;
+  const int wpr = k.wpr;
+  const int total = k.h * wpr;
+  int y = k.gtid / wpr, j = k.gtid - y * wpr;
+  const int dy = k.gthreads / wpr, dj = k.gthreads - dy * wpr;
   for (int t = k.gtid; t < total; t += k.gthreads) {
-    const int y = t / k.wpr, j = t - y * k.wpr;
-    const int id = k.idx(y, j);
+    const int yy = y, jj = j;
+    y += dy;
+    j += dj;
+    if (j >= wpr) {
+      j -= wpr;
+      ++y;
+    }
+    const int id = k.idx(yy, jj);
     const uint32_t s = Mode::ld(k.S + id);
     const uint32_t cd = Mode::ld(k.cand + id);
-    uint32_t allow = thin ? s : (~s & k.rowmask(j));
-    if (pos) allow &= Mode::ld(pos + t);
-    if (neg) allow &= ~Mode::ld(neg + t);
-    const uint32_t pend = allow & ~cd;
+    uint32_t pend = (thin ? s : (~s & k.rowmask(jj))) & ~cd;
+    if (!pend) continue;
+    if (pos) pend &= Mode::ld(pos + t);
+    if (neg) pend &= ~Mode::ld(neg + t);
     if (!pend) continue;
     uint32_t ring = 0;
     for (int o = o0; o < o1; ++o) {
-      ring |= fshift(k, k.F, y + c_lv.off[o][1], j, c_lv.off[o][0], cm, cm);
+      ring |= fshift(k, k.F, yy + c_lv.off[o][1], jj, c_lv.off[o][0], cm, cm);
       ++k.n_ring;
       if (!(pend & ~ring)) break;
     }
@@ -223,35 +274,84 @@ __device__ int level_update(Ctx<Mode>& k, int li, bool thin, const uint32_t* pos
   return k.m.sync_or(act);
 }
 
+// Test the padded-plane word `id` in the subfield with column mask pm and
+// change its simple candidates.
+template <class Mode, int CONN>
+__device__ __forceinline__ void test_word(Ctx<Mode>& k, int id, uint32_t pm, bool thin,
+                                          int& any) {
+  const int P = k.P;
+  uint32_t* S = k.S;
+  const uint32_t cw = Mode::ld(k.cand + id);
+  ++k.n_tests;
+  const uint32_t ctr = Mode::ld(S + id);
+  const uint32_t sm = simple_bits<CONN>(
+      Mode::ld(S + id - P - 1), Mode::ld(S + id - P), Mode::ld(S + id - P + 1),
+      Mode::ld(S + id - 1), ctr, Mode::ld(S + id + 1),
+      Mode::ld(S + id + P - 1), Mode::ld(S + id + P), Mode::ld(S + id + P + 1));
+  const uint32_t chg = cw & pm & sm;
+  if (chg) {
+    Mode::st(S + id, thin ? (ctr & ~chg) : (ctr | chg));
+    Mode::st(k.cand + id, cw & ~chg);
+    any = 1;
+  }
+}
+
 // One subfield pass: change every candidate of the subfield that is simple.
+// Each lane scans one word per step (a row of this pass's parity); a ballot
+// compacts the words holding candidates of the subfield into a per-warp
+// queue (two registers per lane: positions lane and 32 + lane), and the 3 x 3
+// test runs on full batches of 32 queued words, so that its lanes all do
+// useful work.  Points of one subfield are never 8-adjacent: the order in
+// which words are tested does not matter.
 template <class Mode, int CONN>
 __device__ __forceinline__ int sweep_subfield(Ctx<Mode>& k, int sub, bool thin) {
   const int sy = sub >> 1;
   const uint32_t pm = (sub & 1) ? 0xAAAAAAAAu : 0x55555555u;
   const int nrows = (k.h - sy + 1) >> 1;
-  const int total = nrows * k.wpr;
-  const int P = k.P;
-  uint32_t* S = k.S;
+  const int wpr = k.wpr;
+  const int total = nrows * wpr;
+  const int lane = threadIdx.x & 31;
   int any = 0;
-  for (int t = k.gtid; t < total; t += k.gthreads) {
-    const int i = t / k.wpr, j = t - i * k.wpr;
-    const int id = k.idx(sy + 2 * i, j);
-    const uint32_t cw = Mode::ld(k.cand + id);
-    const uint32_t c = cw & pm;
-    if (!c) continue;
-    ++k.n_tests;
-    const uint32_t ctr = Mode::ld(S + id);
-    const uint32_t sm = simple_bits<CONN>(
-        Mode::ld(S + id - P - 1), Mode::ld(S + id - P), Mode::ld(S + id - P + 1),
-        Mode::ld(S + id - 1), ctr, Mode::ld(S + id + 1),
-        Mode::ld(S + id + P - 1), Mode::ld(S + id + P), Mode::ld(S + id + P + 1));
-    const uint32_t chg = c & sm;
-    if (chg) {
-      Mode::st(S + id, thin ? (ctr & ~chg) : (ctr | chg));
-      Mode::st(k.cand + id, cw & ~chg);
-      any = 1;
+  int q0 = 0, q1 = 0;  // queued word indices
+  int qn = 0;          // queue length (warp-uniform)
+  // word t of this pass = parity row t / wpr, word t % wpr; warps take 32
+  // consecutive words per step
+  const int stride = k.nwarps * 32;
+  int t = k.wid * 32 + lane;
+  int i = t / wpr, j = t - i * wpr;
+  const int di = stride / wpr, dj = stride - di * wpr;
+  const int P2 = 2 * k.P;
+  for (int t0 = k.wid * 32; t0 < total; t0 += stride) {   // warp-uniform loop
+    int id = -1;
+    if (t < total) {
+      const int w = k.idx(sy + 2 * i, j);
+      if (Mode::ld(k.cand + w) & pm) id = w;
+    }
+    t += stride;
+    i += di;
+    j += dj;
+    if (j >= wpr) {
+      j -= wpr;
+      ++i;
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, id >= 0);
+    if (!bal) continue;
+    const int nnew = __popc(bal);
+    const int p0 = lane - qn, p1 = lane + 32 - qn;
+    const bool take0 = p0 >= 0 && p0 < nnew, take1 = p1 >= 0 && p1 < nnew;
+    const int v0 = __shfl_sync(0xFFFFFFFFu, id, take0 ? __fns(bal, 0, p0 + 1) : 0);
+    const int v1 = __shfl_sync(0xFFFFFFFFu, id, take1 ? __fns(bal, 0, p1 + 1) : 0);
+    if (take0) q0 = v0;
+    if (take1) q1 = v1;
+    qn += nnew;
+    if (qn >= 32) {
+      test_word<Mode, CONN>(k, q0, pm, thin, any);
+      q0 = q1;
+      qn -= 32;
     }
   }
+  (void)P2;
+  if (lane < qn) test_word<Mode, CONN>(k, q0, pm, thin, any);
   return any;
 }
 
@@ -310,8 +410,8 @@ __device__ void snapshot(Ctx<Mode>& k, uint32_t* g0) {
 // Zero the three padded planes, then pack the input (and C, D) into them.
 template <class Mode>
 __device__ void load_job(Ctx<Mode>& k, const Job& jb, uint32_t* planes_base) {
-  const int pw = jb.plane_words;
-  for (int t = k.gtid; t < 3 * pw; t += k.gthreads) Mode::st(planes_base + t, 0u);
+  const int nw = 3 * jb.plane_words + dirty_words(jb.w, jb.h);
+  for (int t = k.gtid; t < nw; t += k.gthreads) Mode::st(planes_base + t, 0u);
   k.m.sync();
   const int lane = threadIdx.x & 31;
   const int gwarp = k.gtid >> 5, nwarps = k.gthreads >> 5;
@@ -409,14 +509,27 @@ __device__ __forceinline__ void init_ctx(Ctx<Mode>& k, const Job& jb, uint32_t* 
   k.w = jb.w;
   k.h = jb.h;
   k.wpr = jb.wpr;
-  k.P = jb.wpr + 1;
+  k.P = row_pitch(jb.w);
+  k.dwpr = (jb.wpr + 31) >> 5;
   const int rem = jb.w & 31;
   k.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
   k.S = base + 1;
   k.F = base + jb.plane_words + 1;
   k.cand = base + 2 * jb.plane_words + 1;
+  k.dirty = base + 3 * jb.plane_words;
   k.gtid = gtid;
   k.gthreads = gthreads;
+  k.wid = gtid >> 5;
+  k.nwarps = gthreads >> 5;
+  int L = 1;
+  while (L < jb.wpr && L < 32) L <<= 1;
+  k.L = L;
+  const int lane = threadIdx.x & 31;
+  k.grp = lane / L;
+  k.lj = lane % L;
+  k.nchunks = jb.wpr > 32 ? (jb.wpr + 31) >> 5 : 1;
+  walk_init(k.walk1, 1, L, 32 / L, k.P, k.wid, k.nwarps);
+  walk_init(k.walk2, 2, L, 32 / L, k.P, k.wid, k.nwarps);
   k.cap = jb.cap;
   k.n_tests = k.n_ring = k.n_passes = k.n_levels = k.n_rounds = 0;
 }
@@ -459,6 +572,12 @@ hasf_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) 
   else run_job<GangMode, 8>(k, jb, jb.planes);
 }
 
+}  // namespace hasf
+
+#include "hasf_reg.cuh"
+
+namespace hasf {
+
 // All 256 neighbour codes through simple_bits: thread t builds the 3 x 3
 // words whose bit 1 holds the code t's neighbourhood and reads bit 1.
 __global__ void simple_table_kernel(int conn, uint8_t* out) {
@@ -482,7 +601,7 @@ __global__ void simple_table_kernel(int conn, uint8_t* out) {
 __global__ void levels_pack_kernel(const uint8_t* feat, int w, int h, int pitch, uint32_t* Fp,
                                    uint32_t pad) {
   const int wpr = words_per_row(w);
-  const int P = wpr + 1;
+  const int P = row_pitch(w);
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -501,7 +620,7 @@ __global__ void levels_walk_kernel(int w, int h, int mode, int r, const uint32_t
   k.w = w;
   k.h = h;
   k.wpr = words_per_row(w);
-  k.P = k.wpr + 1;
+  k.P = row_pitch(w);
   const int rem = w & 31;
   k.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
   const uint32_t inv = mode == 2 ? 0xFFFFFFFFu : 0u;
@@ -598,6 +717,27 @@ int resident_ctas_per_sm(int device, size_t smem_bytes) {
                        (int)smem_bytes);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hasf_resident_kernel, kThreads, smem_bytes);
   return n;
+}
+
+size_t reg_kernel_smem(int w, int h) { return reg_smem_bytes(w, h); }
+bool reg_kernel_ok(int w, int h) { return reg_kernel_fits(w, h); }
+
+int reg_ctas_per_sm(size_t smem_bytes) {
+  int n = 0;
+  cudaFuncSetAttribute(hasf_reg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem_bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hasf_reg_kernel, kThreads, smem_bytes);
+  return n;
+}
+
+cudaError_t launch_reg(const Job* d_jobs, const int* d_order, int njobs, int grid,
+                       size_t smem_bytes, unsigned* d_counter, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(hasf_reg_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  hasf_reg_kernel<<<grid, kThreads, smem_bytes, s>>>(d_jobs, d_order, njobs, d_counter);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, int grid,
