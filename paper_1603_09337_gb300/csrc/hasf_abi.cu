@@ -211,7 +211,7 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
       off += align_up(state_bytes(im.width, im.height));
       j.sync = base ? (unsigned*)(base + p.off_sync) + 8 * i : nullptr;
       p.gang_jobs.push_back(i);
-    } else if (!ctx->opt.generic_only && reg_kernel_ok(im.width, im.height)) {
+    } else if (!ctx->opt.generic_only && reg_kernel_ok(im.width, im.height, im.rmax)) {
       j.gang = 1;
       p.reg_order.push_back(i);
       p.reg_smem = std::max(p.reg_smem, reg_kernel_smem(im.width, im.height));

@@ -84,7 +84,7 @@ cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, in
                             size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
 cudaError_t launch_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);
 size_t reg_kernel_smem(int w, int h);
-bool reg_kernel_ok(int w, int h);
+bool reg_kernel_ok(int w, int h, int rmax);
 int reg_ctas_per_sm(size_t smem_bytes);
 cudaError_t launch_reg(const Job* d_jobs, const int* d_order, int njobs, int grid,
                        size_t smem_bytes, unsigned* d_counter, cudaStream_t s);

@@ -720,7 +720,7 @@ int resident_ctas_per_sm(int device, size_t smem_bytes) {
 }
 
 size_t reg_kernel_smem(int w, int h) { return reg_smem_bytes(w, h); }
-bool reg_kernel_ok(int w, int h) { return reg_kernel_fits(w, h); }
+bool reg_kernel_ok(int w, int h, int rmax) { return reg_kernel_fits(w, h, rmax); }
 
 int reg_ctas_per_sm(size_t smem_bytes) {
   int n = 0;

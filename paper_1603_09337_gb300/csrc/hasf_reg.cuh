@@ -31,8 +31,15 @@ constexpr int kRegR = 16;   // rows per thread
 constexpr int kRegRows = kRegR * 2 * (kThreads / 32);  // 512 rows
 constexpr int kRegPitch = kRegW + 1;                    // M and cand row pitch
 
-__host__ __device__ inline bool reg_kernel_fits(int w, int h) {
-  return w <= 32 * kRegW && h <= kRegRows;
+constexpr int kRegPadR = 31;  // zero rows above and below the F plane (rmax <= 31)
+
+__host__ __device__ inline bool reg_kernel_fits(int w, int h, int rmax) {
+  return w <= 32 * kRegW && h <= kRegRows && rmax <= kRegPadR;
+}
+// F plane of the register kernel: rows -kRegPadR .. h + kRegPadR - 1, row pitch
+// row_pitch(w) (the last word of every row is zero), plus one leading word.
+__host__ __device__ inline int reg_f_words(int w, int h) {
+  return (((h + 2 * kRegPadR) * row_pitch(w) + 2) + 3) & ~3;
 }
 // Shared memory: the padded F plane, then M and cand for all kRegRows rows
 // (threads whose rows lie below the image read them: zero), then the
@@ -40,12 +47,12 @@ __host__ __device__ inline bool reg_kernel_fits(int w, int h) {
 constexpr int kRegPlane = kRegRows * kRegPitch;
 constexpr int kRegXchg = 2 * (kThreads / 32) * kRegW;
 __host__ __device__ inline int reg_smem_words(int w, int h) {
-  return plane_words(w, h) + 2 * kRegPlane + kRegXchg;
+  return reg_f_words(w, h) + 2 * kRegPlane + kRegXchg;
 }
 inline size_t reg_smem_bytes(int w, int h) { return (size_t)reg_smem_words(w, h) * 4; }
 
 struct RegCtx {
-  Ctx<SmemMode> g;      // geometry of the padded F plane (and counters)
+  Ctx<SmemMode> g;      // image geometry (and counters); g.F = F at (row 0, word 0)
   uint32_t* M;          // kRegRows rows x kRegPitch words
   uint32_t* cand;       // kRegRows rows x kRegPitch words
   uint32_t* top;        // [warp][kRegW]: first row of each warp
@@ -61,16 +68,27 @@ struct RegCtx {
 // before the next gives the same result as two full passes.  The simple mask
 // of the first test is reused by the second unless a word of the warp's row
 // changed in between; then only the row's own left/right words are
-// re-shuffled.  Warp rows with no candidate are skipped.  Returns the OR of
-// the changed bits.
+// re-shuffled.
+//
+// `need` (warp-uniform, bit q = row q of either strip of the warp) says which
+// rows can change at all.  A row whose last test left it stable stays stable
+// until a row next to it changes or it gains candidates: after the fused test
+// no remaining candidate of the row is simple, except that odd-column changes
+// can re-enable even-column candidates of the same row -- then the row stays
+// marked.  A change in row r marks rows r - 1 and r + 1 (the strips of a warp
+// are stacked, so row 15 and row 0 are neighbours across them).  Returns the
+// OR of the changed bits.
 template <int CONN, int SY>
 __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], bool thin,
-                                             uint32_t above, uint32_t below) {
+                                             uint32_t above, uint32_t below, uint32_t& need) {
   const int j = k.j;
   uint32_t* cr = k.cand + k.s0 * kRegPitch + j;
   uint32_t changed = 0;
+  uint32_t rowchg = 0;  // rows of parity SY that changed (warp-uniform)
+  uint32_t again = 0;   // rows to re-test (odd-column change)
 #pragma unroll
   for (int r = SY; r < kRegR; r += 2) {
+    if (!((need >> r) & 1u)) continue;
     uint32_t cw = cr[r * kRegPitch];
     if (!__any_sync(0xFFFFFFFFu, cw != 0u)) continue;
     const uint32_t n = r > 0 ? S[r - 1] : above;
@@ -86,7 +104,8 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], bo
     if (j == kRegW - 1) ne = e = se = 0u;
     uint32_t sm = simple_bits<CONN>(nw, n, ne, wv, c, e, sw, s, se);
     const uint32_t chg0 = cw & 0x55555555u & sm;
-    if (__any_sync(0xFFFFFFFFu, chg0 != 0u)) {
+    const bool any0 = __any_sync(0xFFFFFFFFu, chg0 != 0u);
+    if (any0) {
       c = thin ? (c & ~chg0) : (c | chg0);
       cw &= ~chg0;
       wv = __shfl_up_sync(0xFFFFFFFFu, c, 1, 16);
@@ -104,33 +123,76 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], bo
       cr[r * kRegPitch] = cw;
       changed |= chg;
     }
+    const bool any1 = __any_sync(0xFFFFFFFFu, chg1 != 0u);
+    if (any0 || any1) rowchg |= 1u << r;
+    if (any1) again |= 1u << r;
   }
+  // rows of this parity were tested: keep only those an odd-column change
+  // may have re-enabled, then mark the neighbours of the changed rows
+  need &= ~(SY ? 0xAAAAu : 0x5555u);
+  need |= again;
+  uint32_t nb = (rowchg << 1) | (rowchg >> 1);
+  if (rowchg & 0x8000u) nb |= 1u;       // row 15 of strip A is above row 0 of strip B
+  if (rowchg & 0x0001u) nb |= 0x8000u;  // and row 0 of strip B below row 15 of strip A
+  need |= nb & 0xFFFFu;
   return changed;
 }
 
 // Rounds at one level until a round changes nothing.  False on the cap.
+// ab_prev / be_prev: the rows across the warp boundary as last seen.
 template <int CONN>
-__device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], bool thin) {
+__device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], bool thin, uint32_t& need,
+                          uint32_t& ab_prev, uint32_t& be_prev) {
   const int lane = threadIdx.x & 31;
   for (int round = 0;; ++round) {
     if (round >= k.g.cap) return false;
     ++k.g.n_rounds;
     k.g.n_passes += 4;
-    k.g.n_tests += kRegR * 2;
     // even rows: row above the strip = last row of the strip above
     uint32_t ab = __shfl_sync(0xFFFFFFFFu, S[kRegR - 1], lane ^ 16);
     if (k.half == 0) ab = k.warp > 0 ? k.bot[(k.warp - 1) * kRegW + k.j] : 0u;
-    uint32_t ch = reg_half<CONN, 0>(k, S, thin, ab, 0u);
+    if (__any_sync(0xFFFFFFFFu, ab != ab_prev)) need |= 1u;
+    ab_prev = ab;
+    k.g.n_tests += 2 * __popc(need & 0x5555u);
+    uint32_t ch = reg_half<CONN, 0>(k, S, thin, ab, 0u, need);
     if (k.half == 0) k.top[k.warp * kRegW + k.j] = S[0];
     __syncthreads();
     // odd rows: row below the strip = first row of the strip below
     uint32_t be = __shfl_sync(0xFFFFFFFFu, S[0], lane ^ 16);
     if (k.half == 1)
       be = (k.warp + 1) < (int)(blockDim.x >> 5) ? k.top[(k.warp + 1) * kRegW + k.j] : 0u;
-    ch |= reg_half<CONN, 1>(k, S, thin, 0u, be);
+    if (__any_sync(0xFFFFFFFFu, be != be_prev)) need |= 0x8000u;
+    be_prev = be;
+    k.g.n_tests += 2 * __popc(need & 0xAAAAu);
+    ch |= reg_half<CONN, 1>(k, S, thin, 0u, be, need);
     if (k.half == 1) k.bot[k.warp * kRegW + k.j] = S[kRegR - 1];
     if (!__syncthreads_or(ch != 0u)) return true;
   }
+}
+
+// Points of priority <= the current level among `pend`: the feature plane
+// shifted by each vector of the level, ORed.  A thinning's feature set is the
+// complement of F (outside the box included: the zero padding and the zero
+// bits past the width read as feature), so it ANDs F and complements at the
+// end.  No bounds checks: the padding covers |dy| <= 31, |dx| <= 32.
+template <bool THIN>
+__device__ __forceinline__ uint32_t reg_ring(const uint32_t* F, int P, int y, int j, int o0,
+                                             int o1, uint32_t pend, unsigned& nring) {
+  const uint32_t* base = F + y * P + j;
+  uint32_t acc = THIN ? 0xFFFFFFFFu : 0u;
+  int o = o0;
+  for (; o < o1; ++o) {
+    const int dx = c_lv.off[o][0], dy = c_lv.off[o][1];
+    const uint32_t* q = base + dy * P + (dx >> 5);
+    const uint32_t v = __funnelshift_r(q[0], q[1], dx & 31);
+    acc = THIN ? (acc & v) : (acc | v);
+    if (((o - o0) & 3) == 3 && !(pend & ~(THIN ? ~acc : acc))) {
+      ++o;
+      break;
+    }
+  }
+  nring += o - o0;
+  return THIN ? ~acc : acc;
 }
 
 // One constrained thinning (thin) or thickening at radius r; the allowed
@@ -139,18 +201,20 @@ template <int CONN>
 __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r, bool thin,
                              const uint32_t* pos, const uint32_t* neg) {
   Ctx<SmemMode>& g = k.g;
-  // snapshot F, the movable mask M, no candidates
+  // snapshot F, the movable mask M, no candidates; rows with movable points
+  uint32_t pendrows = 0;
 #pragma unroll
   for (int q = 0; q < kRegR; ++q) {
     const int y = k.s0 + q;
     if (y < g.h) {
       uint32_t m = 0;
       if (k.jin) {
-        g.F[g.idx(y, k.j)] = S[q];
+        g.F[y * g.P + k.j] = S[q];
         const int t = y * g.wpr + k.j;
         m = g.rowmask(k.j);
         if (pos) m &= pos[t];
         if (neg) m &= ~neg[t];
+        if (m & (thin ? S[q] : ~S[q])) pendrows |= 1u << q;
       }
       k.M[y * kRegPitch + k.j] = m;
       k.cand[y * kRegPitch + k.j] = 0u;
@@ -160,71 +224,94 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r, bool thin,
   if (k.half == 0) k.top[k.warp * kRegW + k.j] = S[0];
   if (k.half == 1) k.bot[k.warp * kRegW + k.j] = S[kRegR - 1];
   __syncthreads();
-  const uint32_t cm = thin ? 0xFFFFFFFFu : 0u;
+  uint32_t need = 0;
+  const int lane = threadIdx.x & 31;
+  uint32_t ab_prev = __shfl_sync(0xFFFFFFFFu, S[kRegR - 1], lane ^ 16);
+  if (k.half == 0) ab_prev = k.warp > 0 ? k.bot[(k.warp - 1) * kRegW + k.j] : 0u;
+  uint32_t be_prev = __shfl_sync(0xFFFFFFFFu, S[0], lane ^ 16);
+  if (k.half == 1)
+    be_prev = (k.warp + 1) < (int)(blockDim.x >> 5) ? k.top[(k.warp + 1) * kRegW + k.j] : 0u;
   const int nlev = c_lv.nlev[r];
   for (int li = 0; li < nlev; ++li) {
     const int o0 = c_lv.start[li], o1 = c_lv.start[li + 1];
-    uint32_t act = 0;
+    uint32_t newrows = 0;
 #pragma unroll
     for (int q = 0; q < kRegR; ++q) {
+      if (!((pendrows >> q) & 1u)) continue;
       const int y = k.s0 + q;
-      if (y >= g.h || !k.jin) continue;
       const int a = y * kRegPitch + k.j;
       const uint32_t cd = k.cand[a];
-      uint32_t pend = k.M[a] & (thin ? S[q] : ~S[q]) & ~cd;
-      if (!pend) continue;
-      uint32_t ring = 0;
-      for (int o = o0; o < o1; ++o) {
-        ring |= fshift(g, g.F, y + c_lv.off[o][1], k.j, c_lv.off[o][0], cm, cm);
-        ++g.n_ring;
-        if (!(pend & ~ring)) break;
+      const uint32_t pend = k.M[a] & (thin ? S[q] : ~S[q]) & ~cd;
+      if (!pend) {
+        pendrows &= ~(1u << q);
+        continue;
       }
+      const uint32_t ring = thin ? reg_ring<true>(g.F, g.P, y, k.j, o0, o1, pend, g.n_ring)
+                                 : reg_ring<false>(g.F, g.P, y, k.j, o0, o1, pend, g.n_ring);
       const uint32_t add = pend & ring;
       if (add) {
         k.cand[a] = cd | add;
-        act = 1;
+        newrows |= 1u << q;
+        if (!(pend & ~add)) pendrows &= ~(1u << q);
       }
     }
-    if (!__syncthreads_or(act != 0u)) continue;
+    need |= __reduce_or_sync(0xFFFFFFFFu, newrows);
+    if (!__syncthreads_or(newrows != 0u)) continue;
     ++g.n_levels;
-    if (!reg_level<CONN>(k, S, thin)) return false;
+    if (!reg_level<CONN>(k, S, thin, need, ab_prev, be_prev)) return false;
   }
   return true;
+}
+
+// 1 bit per byte (non-zero = 1) of n <= 32 bytes at p.
+__device__ __forceinline__ uint32_t nibbles(uint32_t x) {
+  uint32_t t = (x | (x >> 4)) & 0x0F0F0F0Fu;
+  t = (t | (t >> 2)) & 0x03030303u;
+  t = (t | (t >> 1)) & 0x01010101u;
+  return (t * 0x01020408u) >> 24;  // byte i's bit to bit i
+}
+__device__ __forceinline__ uint32_t pack_word(const uint8_t* p, int n, bool vec) {
+  if (vec && n == 32) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(p) + 1);
+    return nibbles(a.x) | (nibbles(a.y) << 4) | (nibbles(a.z) << 8) | (nibbles(a.w) << 12) |
+           (nibbles(b.x) << 16) | (nibbles(b.y) << 20) | (nibbles(b.z) << 24) |
+           (nibbles(b.w) << 28);
+  }
+  uint32_t v = 0;
+  for (int i = 0; i < n; ++i) v |= (p[i] != 0 ? 1u : 0u) << i;
+  return v;
 }
 
 template <int CONN>
 __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
   Ctx<SmemMode>& g = k.g;
   uint32_t S[kRegR];
-  // pack the input (and C, D) through the F plane
+  // zero the shared planes, then read this thread's 16 words straight from
+  // the input (32 bytes per word: two 16-byte loads when rows are aligned)
   {
     const int nz = reg_smem_words(jb.w, jb.h);
     for (int t = threadIdx.x; t < nz; t += blockDim.x) smem[t] = 0u;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int total = g.h * g.wpr;
+    const bool vec = ((reinterpret_cast<uintptr_t>(jb.in) | (uintptr_t)jb.pitch |
+                       reinterpret_cast<uintptr_t>(jb.C) | reinterpret_cast<uintptr_t>(jb.D)) &
+                      15u) == 0;
     const bool cx = jb.op == OP_HASF || jb.op == OP_HC;
-    for (int it = wid; it < total; it += nw) {
-      const int y = it / g.wpr, j = it - y * g.wpr;
-      const int x = (j << 5) + lane;
-      const bool inb = x < g.w;
-      const size_t off = (size_t)y * jb.pitch + x;
-      const uint32_t xs = __ballot_sync(0xFFFFFFFFu, inb && jb.in[off] != 0);
-      uint32_t cs = 0, ds = 0;
-      if (jb.cp) cs = __ballot_sync(0xFFFFFFFFu, inb && jb.C != nullptr && jb.C[off] != 0);
-      if (jb.dp) ds = __ballot_sync(0xFFFFFFFFu, inb && jb.D != nullptr && jb.D[off] != 0);
-      if (lane == 0) {
-        g.F[g.idx(y, j)] = xs;
-        if (jb.cp) jb.cp[it] = cx ? (cs & xs) : cs;
-        if (jb.dp) jb.dp[it] = ds & ~xs;
-      }
-    }
-    __syncthreads();
 #pragma unroll
     for (int q = 0; q < kRegR; ++q) {
       const int y = k.s0 + q;
-      S[q] = (y < g.h && k.jin) ? g.F[g.idx(y, k.j)] : 0u;
+      uint32_t xs = 0;
+      if (y < g.h && k.jin) {
+        const size_t off = (size_t)y * jb.pitch + (k.j << 5);
+        const int n = min(32, g.w - (k.j << 5));
+        xs = pack_word(jb.in + off, n, vec);
+        const int t = y * g.wpr + k.j;
+        if (jb.cp) {
+          const uint32_t cs = jb.C ? pack_word(jb.C + off, n, vec) : 0u;
+          jb.cp[t] = cx ? (cs & xs) : cs;
+        }
+        if (jb.dp) jb.dp[t] = (jb.D ? pack_word(jb.D + off, n, vec) : 0u) & ~xs;
+      }
+      S[q] = xs;
     }
     __syncthreads();
   }
@@ -327,11 +414,11 @@ hasf_reg_kernel(const Job* __restrict__ jobs, const int* __restrict__ order, int
     const int rem = jb.w & 31;
     g.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
     g.S = nullptr;
-    g.F = smem + 1;
+    g.F = smem + 1 + kRegPadR * g.P;
     g.cand = nullptr;
     g.cap = jb.cap;
     g.n_tests = g.n_ring = g.n_passes = g.n_levels = g.n_rounds = 0;
-    k.M = smem + jb.plane_words;
+    k.M = smem + reg_f_words(jb.w, jb.h);
     k.cand = k.M + kRegPlane;
     k.top = k.cand + kRegPlane;
     k.bot = k.top + (kThreads / 32) * kRegW;
