@@ -84,7 +84,7 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], bo
   const int j = k.j;
   uint32_t* cr = k.cand + k.s0 * kRegPitch + j;
   uint32_t changed = 0;
-  uint32_t rowchg = 0;  // rows of parity SY that changed (warp-uniform)
+  uint32_t rowchg = 0;  // rows of parity SY that changed (made warp-uniform below)
   uint32_t again = 0;   // rows to re-test (odd-column change)
 #pragma unroll
   for (int r = SY; r < kRegR; r += 2) {
@@ -123,10 +123,11 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], bo
       cr[r * kRegPitch] = cw;
       changed |= chg;
     }
-    const bool any1 = __any_sync(0xFFFFFFFFu, chg1 != 0u);
-    if (any0 || any1) rowchg |= 1u << r;
-    if (any1) again |= 1u << r;
+    if (any0 || chg1) rowchg |= 1u << r;
+    if (chg1) again |= 1u << r;
   }
+  rowchg = __reduce_or_sync(0xFFFFFFFFu, rowchg);
+  again = __reduce_or_sync(0xFFFFFFFFu, again);
   // rows of this parity were tested: keep only those an odd-column change
   // may have re-enabled, then mark the neighbours of the changed rows
   need &= ~(SY ? 0xAAAAu : 0x5555u);
@@ -170,30 +171,12 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], bool thin, uint32_t& 
   }
 }
 
-// Points of priority <= the current level among `pend`: the feature plane
-// shifted by each vector of the level, ORed.  A thinning's feature set is the
+// Level updates read the feature plane F (the operator's input snapshot)
+// shifted by each vector of the level and OR the words: a point reached by a
+// vector of squared norm l has priority <= l.  A thinning's feature set is the
 // complement of F (outside the box included: the zero padding and the zero
 // bits past the width read as feature), so it ANDs F and complements at the
 // end.  No bounds checks: the padding covers |dy| <= 31, |dx| <= 32.
-template <bool THIN>
-__device__ __forceinline__ uint32_t reg_ring(const uint32_t* F, int P, int y, int j, int o0,
-                                             int o1, uint32_t pend, unsigned& nring) {
-  const uint32_t* base = F + y * P + j;
-  uint32_t acc = THIN ? 0xFFFFFFFFu : 0u;
-  int o = o0;
-  for (; o < o1; ++o) {
-    const int dx = c_lv.off[o][0], dy = c_lv.off[o][1];
-    const uint32_t* q = base + dy * P + (dx >> 5);
-    const uint32_t v = __funnelshift_r(q[0], q[1], dx & 31);
-    acc = THIN ? (acc & v) : (acc | v);
-    if (((o - o0) & 3) == 3 && !(pend & ~(THIN ? ~acc : acc))) {
-      ++o;
-      break;
-    }
-  }
-  nring += o - o0;
-  return THIN ? ~acc : acc;
-}
 
 // One constrained thinning (thin) or thickening at radius r; the allowed
 // points are (thin ? S : complement of S) cap pos minus neg (global planes).
@@ -236,23 +219,53 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r, bool thin,
     const int o0 = c_lv.start[li], o1 = c_lv.start[li + 1];
     uint32_t newrows = 0;
 #pragma unroll
-    for (int q = 0; q < kRegR; ++q) {
-      if (!((pendrows >> q) & 1u)) continue;
-      const int y = k.s0 + q;
-      const int a = y * kRegPitch + k.j;
-      const uint32_t cd = k.cand[a];
-      const uint32_t pend = k.M[a] & (thin ? S[q] : ~S[q]) & ~cd;
-      if (!pend) {
-        pendrows &= ~(1u << q);
-        continue;
+    for (int g4 = 0; g4 < kRegR; g4 += 4) {
+      if (!((pendrows >> g4) & 0xFu)) continue;
+      uint32_t pend[4], acc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = g4 + u;
+        pend[u] = 0u;
+        if ((pendrows >> q) & 1u) {
+          const int a = (k.s0 + q) * kRegPitch + k.j;
+          pend[u] = k.M[a] & (thin ? S[q] : ~S[q]) & ~k.cand[a];
+          if (!pend[u]) pendrows &= ~(1u << q);
+        }
+        acc[u] = thin ? 0xFFFFFFFFu : 0u;
       }
-      const uint32_t ring = thin ? reg_ring<true>(g.F, g.P, y, k.j, o0, o1, pend, g.n_ring)
-                                 : reg_ring<false>(g.F, g.P, y, k.j, o0, o1, pend, g.n_ring);
-      const uint32_t add = pend & ring;
-      if (add) {
-        k.cand[a] = cd | add;
-        newrows |= 1u << q;
-        if (!(pend & ~add)) pendrows &= ~(1u << q);
+      if (!(pend[0] | pend[1] | pend[2] | pend[3])) continue;
+      // the level's vectors, applied to the four rows at once (independent
+      // chains); stop once every pending point of the four rows is reached
+      const uint32_t* base = g.F + (k.s0 + g4) * g.P + k.j;
+      for (int o = o0; o < o1; ++o) {
+        const int dx = c_lv.off[o][0], dy = c_lv.off[o][1];
+        const uint32_t* p0 = base + dy * g.P + (dx >> 5);
+        const int sh = dx & 31;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (pend[u]) {  // rows without pending points may lie past the image
+            const uint32_t v = __funnelshift_r(p0[u * g.P], p0[u * g.P + 1], sh);
+            acc[u] = thin ? (acc[u] & v) : (acc[u] | v);
+          }
+        }
+        ++g.n_ring;
+        if (((o - o0) & 3) == 3) {
+          uint32_t left = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) left |= pend[u] & (thin ? acc[u] : ~acc[u]);
+          if (!left) break;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t add = pend[u] & (thin ? ~acc[u] : acc[u]);
+        if (add) {
+          const int q = g4 + u;
+          const int a = (k.s0 + q) * kRegPitch + k.j;
+          k.cand[a] |= add;
+          newrows |= 1u << q;
+          if (!(pend[u] & ~add)) pendrows &= ~(1u << q);
+        }
       }
     }
     need |= __reduce_or_sync(0xFFFFFFFFu, newrows);
