@@ -282,3 +282,51 @@ def test_budget_too_small(ctx):
         assert e.value.code == _lib.HASF_EBUDGET
     finally:
         small.close()
+
+
+# --- large images (gang mode) and ragged batches ---------------------------------------
+
+def _counts(X):
+    from tests import _brute as B
+    return B.component_counts(X)
+
+
+def test_large_image_exact_2048(ctx):
+    """A 2048 x 2048 image of the large-image workload's kind (discs and
+    ellipses of semi-axes 5-200, 3 % noise), rmax 10: too large for one CTA,
+    so it runs in gang mode; equal to the oracle."""
+    X = synth.shapes_image(synth.image_seed(2, 2048), 2048, 2048, 250, 5, 200, n_holes=0,
+                           jitter=0, noise_permille=30)
+    got = host(ctx.smooth(dev(X), 10))
+    ctx.status()
+    np.testing.assert_array_equal(got, oracle.hasf(X, 10))
+
+
+@pytest.mark.parametrize("side", [4096, 8192])
+def test_large_image_full_size_properties(ctx, side):
+    """The 4096^2 / 8192^2 workloads at rmax 10 (the oracle would take minutes):
+    properties that hold at any size -- object and background component counts
+    unchanged, and a second run gives the same bytes."""
+    job = synth.large_image(side)
+    t = dev(job.X)
+    a = host(ctx.smooth(t, job.rmax))
+    b = host(ctx.smooth(t, job.rmax))
+    ctx.status()
+    assert _counts(a) == _counts(job.X)
+    np.testing.assert_array_equal(a, b)
+    assert set(np.unique(a)) <= {0, 1}
+
+
+def test_ragged_batch_sampled(ctx):
+    """A ragged batch of the mixed-size workload (sides 128-2048, rmax 1-8) in
+    one call; its smallest images are checked against the oracle, all images
+    for topology."""
+    from paper_1603_09337_gb300 import Image
+    jobs = synth.ragged_batch(48)
+    imgs = [Image(dev(j.X), j.rmax) for j in jobs]
+    outs = ctx.smooth_batch(imgs)
+    ctx.status()
+    for i in sorted(range(len(jobs)), key=lambda i: jobs[i].X.size)[:5]:
+        np.testing.assert_array_equal(host(outs[i]), oracle.hasf(jobs[i].X, jobs[i].rmax))
+    for j, o in zip(jobs, outs):
+        assert _counts(host(o)) == _counts(j.X)
