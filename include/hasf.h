@@ -174,6 +174,35 @@ int hasf_read_stats(hasf_ctx *ctx, uint64_t *out, int n);
 /* Static description of a status code. */
 const char *hasf_strerror(int status);
 
+/* ---- CUDA graphs ---------------------------------------------------------------
+ * Capture one batched launch of n images into a CUDA graph, for callers that
+ * smooth new contents of the same buffers again and again (video, tiles of a
+ * scan).  The descriptors -- pointers, sizes, rmax, connectivity -- are fixed
+ * when the graph is made; the image bytes are read when it is launched.  The
+ * graph owns its scratch memory (counted against the context's budget) and
+ * must be destroyed before the context.  Errors as hasf_smooth_batch. */
+typedef struct hasf_graph hasf_graph;
+int hasf_graph_create(hasf_ctx *ctx, const hasf_image *imgs, int n, hasf_graph **graph);
+/* Launch the captured work on `stream` (asynchronous). */
+int hasf_graph_launch(hasf_graph *graph, void *stream);
+/* Wait for the graph's launches and free it. */
+int hasf_graph_destroy(hasf_graph *graph);
+
+/* ---- Autotuner --------------------------------------------------------------
+ * Images that do not fit the register kernel run either in the generic
+ * shared-memory kernel (one CTA) or in gang mode (several CTAs sharing planes
+ * in L2).  hasf_autotune times the candidates -- the one-CTA kernel when the
+ * image fits it, and gangs of 1, 2, 4, ... CTAs -- on a synthetic image of
+ * the given size, in batches that fill the GPU (throughput, the batched
+ * use), and records the fastest for the size bucket (powers of two of width
+ * and height, and rmax).  Later batches use the recorded choice.
+ * *ctas receives the choice (0 = one-CTA kernel).  Synchronous. */
+int hasf_autotune(hasf_ctx *ctx, int32_t width, int32_t height, int32_t rmax,
+                  int32_t connectivity, int32_t *ctas);
+/* Save / load the tuned choices as text ("log2w log2h rmax ctas" lines). */
+int hasf_tuning_save(hasf_ctx *ctx, const char *path);
+int hasf_tuning_load(hasf_ctx *ctx, const char *path);
+
 /* ---- Single operators (the same kernels, one step of the filter) --------- */
 
 /* Exact squared Euclidean distance transform (Sec. 4.1, Meijster's two

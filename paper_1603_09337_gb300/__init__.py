@@ -187,6 +187,34 @@ class Context:
               "hasf_simple_table")
         return out
 
+    # -- CUDA graphs and the autotuner --------------------------------------------
+    def graph_create(self, images: list[Image]):
+        """Capture one batched launch of `images` (buffers fixed) as a CUDA graph."""
+        arr = self.batch_descriptors(images)
+        g = ctypes.c_void_p()
+        check(self.lib.hasf_graph_create(self.h, arr, len(images), ctypes.byref(g)),
+              "hasf_graph_create")
+        return g
+
+    def graph_launch(self, graph, stream=None):
+        check(self.lib.hasf_graph_launch(graph, _stream_handle(stream)), "hasf_graph_launch")
+
+    def graph_destroy(self, graph):
+        check(self.lib.hasf_graph_destroy(graph), "hasf_graph_destroy")
+
+    def autotune(self, width: int, height: int, rmax: int, conn: int = 8) -> int:
+        """Time the launch shapes for this size bucket; returns CTAs per image (0 = one CTA)."""
+        c = ctypes.c_int32()
+        check(self.lib.hasf_autotune(self.h, width, height, rmax, conn, ctypes.byref(c)),
+              "hasf_autotune")
+        return c.value
+
+    def tuning_save(self, path: str):
+        check(self.lib.hasf_tuning_save(self.h, path.encode()), "hasf_tuning_save")
+
+    def tuning_load(self, path: str):
+        check(self.lib.hasf_tuning_load(self.h, path.encode()), "hasf_tuning_load")
+
     # -- host-buffer entry point -----------------------------------------------
     def smooth_host(self, jobs):
         """jobs: list of (X numpy (h, w) uint8, rmax, C or None, D or None, conn, out numpy)."""

@@ -28,7 +28,9 @@ EXPORTS = (
     "hasf_create", "hasf_destroy", "hasf_smooth", "hasf_smooth_batch", "hasf_status_of",
     "hasf_smooth_host", "hasf_submit", "hasf_poll", "hasf_cancel", "hasf_drain",
     "hasf_set_option", "hasf_strerror", "hasf_edt", "hasf_operator", "hasf_simple_table",
-    "hasf_levels", "hasf_read_stats", "hasf_smooth_noalloc",
+    "hasf_levels", "hasf_read_stats", "hasf_smooth_noalloc", "hasf_graph_create",
+    "hasf_graph_launch", "hasf_graph_destroy", "hasf_autotune", "hasf_tuning_save",
+    "hasf_tuning_load",
 )
 
 
@@ -81,6 +83,13 @@ def _declare(lib):
                                 ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.hasf_read_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ci]
     lib.hasf_smooth_noalloc.argtypes = [img_p, vp, vp]
+    lib.hasf_graph_create.argtypes = [vp, img_p, ci, ctypes.POINTER(vp)]
+    lib.hasf_graph_launch.argtypes = [vp, vp]
+    lib.hasf_graph_destroy.argtypes = [vp]
+    i32 = ctypes.c_int32
+    lib.hasf_autotune.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(i32)]
+    lib.hasf_tuning_save.argtypes = [vp, ctypes.c_char_p]
+    lib.hasf_tuning_load.argtypes = [vp, ctypes.c_char_p]
     for name in EXPORTS:
         if name != "hasf_strerror":
             getattr(lib, name).restype = ci

@@ -12,8 +12,11 @@
 #include <condition_variable>
 #include <cstdlib>
 #include <cstring>
+#include <cstdio>
 #include <deque>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
@@ -118,6 +121,17 @@ struct hasf_ctx {
   bool stop = false;
   std::thread worker;
   bool worker_running = false;
+
+  // autotuner: size bucket -> CTAs per image (0 = one-CTA generic kernel)
+  std::map<std::tuple<int, int, int>, int> tune;
+};
+
+struct hasf_graph {
+  hasf_ctx* ctx = nullptr;
+  void* mem = nullptr;
+  size_t bytes = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
 };
 
 namespace {
@@ -128,14 +142,31 @@ int cuda_status(cudaError_t e) {
   return HASF_ECUDA;
 }
 
+int ceil_log2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+std::tuple<int, int, int> tune_key(const hasf_image& im) {
+  return std::make_tuple(ceil_log2(im.width), ceil_log2(im.height), im.rmax);
+}
+
+bool fits_resident(const hasf_ctx* ctx, const hasf_image& im) {
+  // keep 1 KB of the per-block limit for the kernel's static shared memory
+  return resident_smem_bytes(im.width, im.height) + 1024 <= ctx->max_smem;
+}
+
 bool wants_gang(const hasf_ctx* ctx, const hasf_image& im) {
   if (ctx->opt.force_gang) return true;
-  // keep 1 KB of the per-block limit for the kernel's static shared memory
-  return resident_smem_bytes(im.width, im.height) + 1024 > ctx->max_smem;
+  if (!fits_resident(ctx, im)) return true;
+  auto it = ctx->tune.find(tune_key(im));
+  return it != ctx->tune.end() && it->second > 0 && !reg_kernel_ok(im.width, im.height, im.rmax);
 }
 
 int gang_size(const hasf_ctx* ctx, const hasf_image& im) {
   if (ctx->opt.gang_ctas > 0) return std::min(ctx->opt.gang_ctas, ctx->gang_max);
+  auto it = ctx->tune.find(tune_key(im));
+  if (it != ctx->tune.end() && it->second > 0) return std::min(it->second, ctx->gang_max);
   const long long words = (long long)im.height * words_per_row(im.width);
   long long g = (words + 4095) / 4096;  // about 8 words per thread and pass
   g = std::max(1LL, std::min(g, (long long)ctx->gang_max));
@@ -240,18 +271,21 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
 }
 
 // Upload the plan's descriptors and launch it on `s`.  `base` is the scratch.
-int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s) {
+int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload = true) {
   const int n = (int)p.jobs.size();
-  std::vector<char> head(p.off_ctamap + sizeof(int2) * std::max<size_t>(p.ctamap.size(), 1), 0);
-  std::memcpy(head.data() + p.off_jobs, p.jobs.data(), sizeof(Job) * n);
-  if (!p.order.empty())
-    std::memcpy(head.data() + p.off_order, p.order.data(), sizeof(int) * p.order.size());
-  if (!p.reg_order.empty())
-    std::memcpy(head.data() + p.off_order + sizeof(int) * p.order.size(), p.reg_order.data(),
-                sizeof(int) * p.reg_order.size());
-  if (!p.ctamap.empty())
-    std::memcpy(head.data() + p.off_ctamap, p.ctamap.data(), sizeof(int2) * p.ctamap.size());
-  cudaError_t e = cudaMemcpyAsync(base, head.data(), head.size(), cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaSuccess;
+  if (upload) {
+    std::vector<char> head(p.off_ctamap + sizeof(int2) * std::max<size_t>(p.ctamap.size(), 1), 0);
+    std::memcpy(head.data() + p.off_jobs, p.jobs.data(), sizeof(Job) * n);
+    if (!p.order.empty())
+      std::memcpy(head.data() + p.off_order, p.order.data(), sizeof(int) * p.order.size());
+    if (!p.reg_order.empty())
+      std::memcpy(head.data() + p.off_order + sizeof(int) * p.order.size(), p.reg_order.data(),
+                  sizeof(int) * p.reg_order.size());
+    if (!p.ctamap.empty())
+      std::memcpy(head.data() + p.off_ctamap, p.ctamap.data(), sizeof(int2) * p.ctamap.size());
+    e = cudaMemcpyAsync(base, head.data(), head.size(), cudaMemcpyHostToDevice, s);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(base + p.off_counter, 0, 16, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + p.off_sync, 0, p.sync_bytes, s);
   if (e != cudaSuccess) return cuda_status(e);
@@ -770,6 +804,198 @@ int hasf_drain(hasf_ctx* ctx) {
   if (!ctx) return HASF_EINVAL;
   std::unique_lock<std::mutex> lk(ctx->mu);
   ctx->cv.wait(lk, [&] { return ctx->pending.empty() && ctx->inflight.empty(); });
+  return HASF_OK;
+}
+
+int hasf_graph_create(hasf_ctx* ctx, const hasf_image* imgs, int n, hasf_graph** out) {
+  if (!ctx || !out || n < 1 || !imgs) return HASF_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    int v = validate(&imgs[i]);
+    if (v) return v;
+  }
+  cudaSetDevice(ctx->device);
+  hasf_graph* g = new (std::nothrow) hasf_graph();
+  if (!g) return HASF_ENOMEM;
+  g->ctx = ctx;
+  Plan p;
+  g->bytes = build_plan(ctx, imgs, n, OP_HASF, p, nullptr, nullptr);
+  if (g->bytes > ctx->budget) {
+    delete g;
+    return HASF_EBUDGET;
+  }
+  cudaError_t e = cudaMalloc(&g->mem, g->bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete g;
+    return HASF_ENOMEM;
+  }
+  build_plan(ctx, imgs, n, OP_HASF, p, (char*)g->mem, ctx->d_status);
+  // Descriptors are fixed: upload them once, outside the capture.
+  cudaStream_t cs = nullptr;
+  e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  int rc = cuda_status(e);
+  if (rc == HASF_OK) rc = launch_plan(ctx, p, (char*)g->mem, cs);  // also warms up
+  if (rc == HASF_OK) rc = cuda_status(cudaStreamSynchronize(cs));
+  if (rc == HASF_OK) rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+  if (rc == HASF_OK) {
+    int lrc = launch_plan(ctx, p, (char*)g->mem, cs, /*upload=*/false);
+    cudaError_t ec = cudaStreamEndCapture(cs, &g->graph);
+    rc = lrc ? lrc : cuda_status(ec);
+  }
+  if (rc == HASF_OK) rc = cuda_status(cudaGraphInstantiate(&g->exec, g->graph, 0));
+  if (cs) cudaStreamDestroy(cs);
+  if (rc != HASF_OK) {
+    cudaGetLastError();
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    cudaFree(g->mem);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return HASF_OK;
+}
+
+int hasf_graph_launch(hasf_graph* g, void* stream) {
+  if (!g) return HASF_EINVAL;
+  cudaSetDevice(g->ctx->device);
+  return cuda_status(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+}
+
+int hasf_graph_destroy(hasf_graph* g) {
+  if (!g) return HASF_EINVAL;
+  cudaSetDevice(g->ctx->device);
+  cudaDeviceSynchronize();
+  cudaGraphExecDestroy(g->exec);
+  cudaGraphDestroy(g->graph);
+  cudaFree(g->mem);
+  delete g;
+  return HASF_OK;
+}
+
+namespace {
+// Synthetic tuning image: discs and 5 % salt-and-pepper from a 64-bit LCG.
+void tune_image(std::vector<uint8_t>& img, int w, int h) {
+  uint64_t st = 0x9E3779B97F4A7C15ull ^ ((uint64_t)w << 32) ^ (uint64_t)h;
+  auto next = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return (uint32_t)(st >> 33);
+  };
+  img.assign((size_t)w * h, 0);
+  const int nd = std::max(1, (int)((long long)w * h / 20000));
+  for (int d = 0; d < nd; ++d) {
+    const int cx = (int)(next() % (uint32_t)w), cy = (int)(next() % (uint32_t)h);
+    const int rr = 5 + (int)(next() % 40u);
+    for (int y = std::max(0, cy - rr); y <= std::min(h - 1, cy + rr); ++y)
+      for (int x = std::max(0, cx - rr); x <= std::min(w - 1, cx + rr); ++x)
+        if ((x - cx) * (x - cx) + (y - cy) * (y - cy) <= rr * rr) img[(size_t)y * w + x] = 1;
+  }
+  for (size_t p = 0; p < img.size(); ++p)
+    if (next() % 100u < 5u) img[p] ^= 1;
+}
+}  // namespace
+
+int hasf_autotune(hasf_ctx* ctx, int32_t width, int32_t height, int32_t rmax, int32_t conn,
+                  int32_t* ctas) {
+  if (!ctx || !ctas || width < 1 || height < 1 || width > 65536 || height > 65536 || rmax < 1 ||
+      rmax > kMaxR || (conn != 4 && conn != 8))
+    return HASF_EINVAL;
+  cudaSetDevice(ctx->device);
+  hasf_image im{};
+  im.width = width;
+  im.height = height;
+  im.pitch = width;
+  im.rmax = rmax;
+  im.connectivity = conn;
+  if (reg_kernel_ok(width, height, rmax)) {  // the register kernel: nothing to choose
+    *ctas = 0;
+    return HASF_OK;
+  }
+  std::vector<uint8_t> host;
+  tune_image(host, width, height);
+  const size_t px = (size_t)width * height;
+  uint8_t* dev = nullptr;
+  // copies run side by side so that each candidate is timed at full occupancy
+  const int copies_max = 16;
+  if (cudaMalloc(&dev, px * 2 * copies_max) != cudaSuccess) {
+    cudaGetLastError();
+    return HASF_ENOMEM;
+  }
+  for (int c = 0; c < copies_max; ++c)
+    cudaMemcpy(dev + px * 2 * c, host.data(), px, cudaMemcpyHostToDevice);
+  std::vector<int> cands;
+  if (fits_resident(ctx, im)) cands.push_back(0);
+  for (int g = 1; g <= ctx->gang_max; g *= 2) cands.push_back(g);
+  const Options saved = ctx->opt;
+  cudaStream_t s = ctx->host_stream;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  double best = 1e30;
+  int best_c = cands.empty() ? 1 : cands.back();
+  int rc = HASF_OK;
+  for (int c : cands) {
+    const int per = c == 0 ? std::max(1, 2 * ctx->num_sms) : std::max(1, ctx->gang_max / c);
+    const int copies = std::min(copies_max, per);
+    std::vector<hasf_image> batch(copies, im);
+    for (int k = 0; k < copies; ++k) {
+      batch[k].in = dev + px * 2 * k;
+      batch[k].out = dev + px * 2 * k + px;
+    }
+    ctx->opt.force_gang = c > 0;
+    ctx->opt.gang_ctas = c;
+    ctx->opt.generic_only = 1;
+    rc = run_images(ctx, batch.data(), copies, OP_HASF, s);  // warm-up
+    if (rc == HASF_OK) rc = hasf_status_of(ctx, s);
+    if (rc != HASF_OK) break;
+    cudaEventRecord(a, s);
+    rc = run_images(ctx, batch.data(), copies, OP_HASF, s);
+    cudaEventRecord(b, s);
+    if (rc == HASF_OK) rc = hasf_status_of(ctx, s);
+    if (rc != HASF_OK) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double per_image = ms / copies;
+    if (per_image < best) {
+      best = per_image;
+      best_c = c;
+    }
+  }
+  ctx->opt = saved;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(dev);
+  if (rc != HASF_OK) return rc;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tune[tune_key(im)] = best_c;
+  }
+  *ctas = best_c;
+  return HASF_OK;
+}
+
+int hasf_tuning_save(hasf_ctx* ctx, const char* path) {
+  if (!ctx || !path) return HASF_EINVAL;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return HASF_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  for (const auto& kv : ctx->tune)
+    std::fprintf(f, "%d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                 std::get<2>(kv.first), kv.second);
+  std::fclose(f);
+  return HASF_OK;
+}
+
+int hasf_tuning_load(hasf_ctx* ctx, const char* path) {
+  if (!ctx || !path) return HASF_EINVAL;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return HASF_EINVAL;
+  int a, b, c, d;
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  while (std::fscanf(f, "%d %d %d %d", &a, &b, &c, &d) == 4)
+    if (a >= 0 && b >= 0 && c >= 1 && c <= kMaxR && d >= 0) ctx->tune[std::make_tuple(a, b, c)] = d;
+  std::fclose(f);
   return HASF_OK;
 }
 
