@@ -1,17 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the HASF library on its headline workload.
 
-Workload (one step): a batch of 256 synthetic 512 x 512 binary images (12
-discs/ellipses, 6 holes, 2-px jitter, 2-10 % salt-and-pepper noise), rmax = 5,
-50 kept points C per image, smoothed by one hasf_smooth_batch launch.
+Workload of one step: a batch of 256 synthetic 512 x 512 binary images (12
+discs/ellipses of semi-axes 20-90, 6 holes, 2-px jitter, 2-10 % salt-and-
+pepper noise), rmax = 5, 50 kept points C per image, smoothed by one
+hasf_smooth_batch launch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hasf|reference]
+                  [--workload batch512|ragged|large] [--serve-seconds S]
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle (the
 plain single-threaded C restatement of the method) on the host cores, as the
 reference arm.  Under torchrun every rank smooths its own batch (replicas, no
 collective on the data path) and the value is all ranks' images over the
-slowest rank's time.
+slowest rank's time.  The line also carries a serving measurement: Poisson
+arrivals at 2,000 requests/s of images of mixed sizes through hasf_submit /
+hasf_poll, p50/p99 latency against plain sequential hasf_smooth calls.
 """
 from __future__ import annotations
 
@@ -31,18 +35,14 @@ BATCH = 256
 RMAX = 5
 WORKLOAD = ("batch of 256 synthetic 512x512 binary images (discs/ellipses, holes, jitter, "
             "2-10% salt-and-pepper), rmax=5, 50 kept points C per image, one batched launch")
-# Lane operations of one word test in the sweep kernel (32 pixels): 10 loads,
-# 6 funnel shifts, 21 logic operations, 4 update operations.
-OPS_PER_WORD_TEST = 41
-# Lane operations of one ring-vector evaluation in a level update.
-OPS_PER_RING_EVAL = 7
-
-
-def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+# Algorithmic lane operations (32 pixels per lane) of the bit-sliced method:
+# one word test = 6 funnel shifts aligning the 8 neighbours, 8 for the four
+# crossing terms, 4 to count exactly one, 2 to gate by the candidates and
+# update the set; one ring read of a level update = 1 funnel shift + 1 OR.
+OPS_PER_WORD_TEST = 20
+OPS_PER_RING_EVAL = 2
+SM_COUNT = 152
+INT32_LANES_PER_SM = 128
 
 
 def _peaks():
@@ -63,18 +63,20 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc is not None:
             time.sleep(0.25)
             self.proc.terminate()
@@ -88,7 +90,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        for l in self.lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -107,7 +109,6 @@ class ClockSampler:
 
 
 def _oracle_job(args):
-    import numpy as np
     import oracle
     X, C, rmax = args
     t = time.perf_counter()
@@ -115,14 +116,17 @@ def _oracle_job(args):
     return time.perf_counter() - t
 
 
-def cpu_oracle_rate(jobs, cores):
-    """Images/s of the oracle on `cores` host processes over `jobs`."""
+def _pool(cores):
     import multiprocessing as mp
     import oracle
     oracle.build()
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
-        pool.map(_oracle_job, [(jobs[0].X, jobs[0].C, jobs[0].rmax)] * cores)  # load in workers
+    return mp.get_context("spawn").Pool(cores)
+
+
+def cpu_oracle_rate(jobs, cores):
+    """Images/s of the oracle on `cores` host processes over `jobs`."""
+    with _pool(cores) as pool:
+        pool.map(_oracle_job, [(jobs[0].X, jobs[0].C, jobs[0].rmax)] * cores)  # warm workers
         t0 = time.perf_counter()
         per = pool.map(_oracle_job, [(j.X, j.C, j.rmax) for j in jobs], chunksize=1)
         wall = time.perf_counter() - t0
@@ -130,18 +134,14 @@ def cpu_oracle_rate(jobs, cores):
 
 
 def run_reference(args):
-    ws, rank, _ = _dist()
+    from paper_1603_09337_gb300 import replicas, synth
+    ws, rank, _ = replicas.world()
     if rank != 0:
         return 0
-    from paper_1603_09337_gb300 import synth
     cores = os.cpu_count() or 1
     per_step = cores
     jobs = synth.batch_512(per_step * (args.steps + args.warmup))
-    import multiprocessing as mp
-    import oracle
-    oracle.build()
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
+    with _pool(cores) as pool:
         k = 0
         for _ in range(args.warmup):
             pool.map(_oracle_job, [(j.X, j.C, j.rmax) for j in jobs[k:k + per_step]], chunksize=1)
@@ -169,25 +169,155 @@ def run_reference(args):
     return 0
 
 
+# --- serving: Poisson arrivals of mixed-size images -----------------------------------
+
+def serving_pool(n: int = 48, seed: int = 4):
+    """Images of the served stream: side lognormal (median 512, sigma 0.5), clipped
+    to [128, 4096], aspect uniform in [0.5, 2], noise 2-10 %."""
+    import math
+    import numpy as np
+    from paper_1603_09337_gb300 import synth
+    rng = synth.SplitMix64(synth.image_seed(4, seed))
+    out = []
+    for i in range(n):
+        u1 = (rng.next() >> 11) / float(1 << 53) or 1e-12
+        u2 = (rng.next() >> 11) / float(1 << 53)
+        z = math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2)
+        s = min(4096.0, max(128.0, 512.0 * math.exp(0.5 * z)))
+        a = 0.5 + 1.5 * (rng.next() >> 11) / float(1 << 53)
+        w = int(min(4096, max(128, round(s * math.sqrt(a)))))
+        h = int(min(4096, max(128, round(s / math.sqrt(a)))))
+        area = w * h
+        X = synth.shapes_image(synth.image_seed(4, 1000 + i), w, h,
+                               max(1, (12 * area + 131072) // 262144), 20,
+                               max(20, min(90, min(w, h) // 3)),
+                               n_holes=(6 * area + 131072) // 262144, jitter=2,
+                               noise_permille=rng.randint(20, 100))
+        out.append(X)
+    return out
+
+
+def run_serving(ctx, dev, seconds: float, rate: float = 2000.0):
+    """Served stream vs plain sequential launches; latency = completion - arrival."""
+    import numpy as np
+    import torch
+    from paper_1603_09337_gb300 import synth
+    pool = serving_pool()
+    ins = [torch.from_numpy(X).to(dev) for X in pool]
+    slots = 8
+    outs = [[torch.empty_like(t) for _ in range(slots)] for t in ins]
+    free = [list(range(slots)) for _ in ins]
+    rng = synth.SplitMix64(0xA77)
+    n = int(rate * seconds)
+    arrivals, picks, rmaxs = [], [], []
+    t = 0.0
+    import math
+    for _ in range(n):
+        u = ((rng.next() >> 11) + 1) / float(1 << 53)
+        t += -math.log(u) / rate
+        arrivals.append(t)
+        picks.append(rng.randint(0, len(pool) - 1))
+        rmaxs.append(rng.randint(1, 6))
+    # warm-up: every image once
+    for i, x in enumerate(ins):
+        ctx.smooth(x, 3, out=outs[i][0])
+    ctx.status()
+
+    def served():
+        lat = []
+        pending = []           # (ticket, arrival, image, slot)
+        waiting = []           # requests that arrived while their image had no free slot
+        t0 = time.perf_counter()
+        k = 0
+        while k < n or pending or waiting:
+            now = time.perf_counter() - t0
+            while k < n and arrivals[k] <= now:
+                waiting.append(k)
+                k += 1
+            still = []
+            for q in waiting:
+                i = picks[q]
+                if free[i]:
+                    sl = free[i].pop()
+                    tk = ctx.submit(ins[i], rmaxs[q], outs[i][sl])
+                    pending.append((tk, arrivals[q], i, sl))
+                else:
+                    still.append(q)
+            waiting = still
+            rest = []
+            for tk, arr, i, sl in pending:
+                done, st = ctx.poll(tk)
+                if done:
+                    lat.append(time.perf_counter() - t0 - arr)
+                    free[i].append(sl)
+                else:
+                    rest.append((tk, arr, i, sl))
+            pending = rest
+        wall = time.perf_counter() - t0
+        return lat, wall
+
+    def sequential(limit_s: float):
+        lat = []
+        t0 = time.perf_counter()
+        for q in range(n):
+            now = time.perf_counter() - t0
+            if now > limit_s:
+                break
+            if arrivals[q] > now:
+                time.sleep(arrivals[q] - now)
+            i = picks[q]
+            ctx.smooth(ins[i], rmaxs[q], out=outs[i][0])
+            ctx.status()
+            lat.append(time.perf_counter() - t0 - arrivals[q])
+        return lat, time.perf_counter() - t0
+
+    s_lat, s_wall = served()
+    q_lat, q_wall = sequential(seconds * 2)
+    pct = lambda a, p: float(np.percentile(np.array(a) * 1e3, p)) if a else None
+    mpx = sum(pool[picks[q]].size for q in range(n)) / 1e6
+    return {
+        "arrival_rate_per_s": rate, "requests": n, "seconds": seconds,
+        "images": f"pool of {len(pool)} images, sides lognormal(median 512, sigma 0.5) in "
+                  "[128, 4096], aspect 0.5-2, noise 2-10%; rmax uniform 1-6 per request",
+        "served": {"p50_ms": pct(s_lat, 50), "p99_ms": pct(s_lat, 99),
+                   "images_per_s": len(s_lat) / s_wall, "mpixel_per_s": mpx / s_wall},
+        "sequential_launches": {"p50_ms": pct(q_lat, 50), "p99_ms": pct(q_lat, 99),
+                                "images_per_s": len(q_lat) / q_wall,
+                                "completed": len(q_lat)},
+    }
+
+
 def run_hasf(args):
     import numpy as np
     import torch
+    from paper_1603_09337_gb300 import Context, Image, build, replicas, synth
 
-    ws, rank, local = _dist()
+    ws, rank, local = replicas.world()
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1603_09337_gb300 import Context, Image, build, synth
-
     build.build()
-    jobs = synth.batch_512(BATCH, first=rank * BATCH)
     ctx = Context(local)
-    X = torch.from_numpy(np.stack([j.X for j in jobs])).to(dev)
-    C = torch.from_numpy(np.stack([j.C for j in jobs])).to(dev)
-    out = torch.empty_like(X)
-    imgs = [Image(X[i], RMAX, C=C[i], out=out[i]) for i in range(BATCH)]
+
+    if args.workload == "batch512":
+        jobs = synth.batch_512(BATCH, first=rank * BATCH)
+        workload, metric = WORKLOAD, METRIC
+    elif args.workload == "ragged":
+        jobs = synth.ragged_batch(args.ragged_n, first=rank * args.ragged_n)
+        workload = (f"ragged batch of {args.ragged_n} images, sides uniform 128-2048, "
+                    "rmax uniform 1-8, one batched launch")
+        metric = "HASF images/s, ragged batch"
+    else:
+        jobs = [synth.large_image(args.side)]
+        workload = f"one {args.side}x{args.side} image of 2,000 discs/ellipses, 3% noise, rmax=10"
+        metric = f"HASF images/s at {args.side}x{args.side}, rmax=10"
+    n = len(jobs)
+    Xs = [torch.from_numpy(j.X).to(dev) for j in jobs]
+    Cs = [torch.from_numpy(j.C).to(dev) if j.C is not None else None for j in jobs]
+    outs = [torch.empty_like(x) for x in Xs]
+    imgs = [Image(Xs[i], jobs[i].rmax, C=Cs[i], out=outs[i]) for i in range(n)]
     arr = ctx.batch_descriptors(imgs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -198,53 +328,54 @@ def run_hasf(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        ctx.smooth_batch_raw(arr, BATCH)
+        ctx.smooth_batch_raw(arr, n)
     ctx.status()
+    stats = ctx.stats_step(arr, n)          # work counters of one step (untimed run)
 
-    # Work counters of one step (for the ALU roofline): a separate, untimed run.
-    stats = ctx.stats_step(arr, BATCH) if hasattr(ctx, "stats_step") else None
-
+    ctx.read_stats()                        # resets the launch counter
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
-    with ClockSampler(torch.cuda.get_device_properties(dev).pci_bus_id if False else local) as clk:
+    with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
         for i in range(args.steps):
-            flush.zero_()                       # evict L2 (129 MB) between steps
+            flush.zero_()                       # evict L2 (129 MB) between steps, untimed
             starts[i].record(stream)
-            ctx.smooth_batch_raw(arr, BATCH)
+            ctx.smooth_batch_raw(arr, n)
             ends[i].record(stream)
         barrier()
         wall = time.perf_counter() - wall0
     ctx.status()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_ms = sum(step_ms)
-    if ws > 1:
-        tt = torch.tensor([t_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    total_images = BATCH * args.steps * ws
-    value = total_images / (t_ms / 1e3)
+    launches = ctx.read_stats()["launches"]   # kernel launches inside the timed region
+    t_ms = replicas.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dev)
+    value = n * args.steps * ws / (t_ms / 1e3)
     ms_per_step = t_ms / args.steps
 
-    # End to end through the host-buffer entry point: H2D + compute + D2H.
+    # End to end through the host-buffer entry point with pinned host buffers:
+    # H2D of X and C, the smoothing, D2H of the result, every step.
     e2e = None
     if not args.no_e2e:
-        hX = [np.ascontiguousarray(j.X) for j in jobs]
-        hC = [np.ascontiguousarray(j.C) for j in jobs]
-        hO = [np.empty_like(j.X) for j in jobs]
-        host_jobs = [(hX[i], RMAX, hC[i], None, 8, hO[i]) for i in range(BATCH)]
-        ctx.smooth_host(host_jobs)                     # warm-up (staging buffers)
+        hX = [torch.from_numpy(j.X).pin_memory().numpy() for j in jobs]
+        hC = [torch.from_numpy(j.C).pin_memory().numpy() if j.C is not None else None
+              for j in jobs]
+        hO = [torch.empty(j.X.shape, dtype=torch.uint8).pin_memory().numpy() for j in jobs]
+        host_jobs = [(hX[i], jobs[i].rmax, hC[i], None, 8, hO[i]) for i in range(n)]
+        ctx.smooth_host(host_jobs)                     # warm-up
         k = max(1, min(args.steps, 5))
         barrier()
         t0 = time.perf_counter()
         for _ in range(k):
             ctx.smooth_host(host_jobs)
         barrier()
-        te = (time.perf_counter() - t0) / k
-        e2e = {"value": BATCH * ws / te, "unit": "images/s",
-               "h2d_bytes_per_step": int(sum(a.nbytes for a in hX) + sum(a.nbytes for a in hC)),
+        te = replicas.max_over_ranks((time.perf_counter() - t0) / k, dev)
+        e2e = {"value": n * ws / te, "unit": "images/s",
+               "h2d_bytes_per_step": int(sum(a.nbytes for a in hX) +
+                                         sum(a.nbytes for a in hC if a is not None)),
                "d2h_bytes_per_step": int(sum(a.nbytes for a in hO))}
+
+    serving = None
+    if rank == 0 and args.serve_seconds > 0 and args.workload == "batch512":
+        serving = run_serving(ctx, dev, args.serve_seconds)
 
     if rank != 0:
         ctx.close()
@@ -253,22 +384,21 @@ def run_hasf(args):
     peaks, peak_src = _peaks()
     clocks = clk.summary()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12            # T lane-ops/s
-    roof = None
-    if stats is not None:
-        ops = stats["word_tests"] * OPS_PER_WORD_TEST + stats["ring_evals"] * OPS_PER_RING_EVAL
-        achieved = ops / (ms_per_step / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": None,
-                "peak_source": "152 SMs x 128 int32 lanes x max SM clock (recipe units/clock)",
-                "ops_per_step": ops, "counters": stats}
-    alg_bytes = BATCH * 512 * 512 * 3
-    hbm = {"achieved_gbs": alg_bytes / (ms_per_step / 1e3) / 1e9, "peak_gbs": peaks["hbm_gbs"],
-           "frac": alg_bytes / (ms_per_step / 1e3) / 1e9 / peaks["hbm_gbs"],
-           "peak_source": peak_src}
+    alu_peak = SM_COUNT * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12      # T lane-ops/s
+    ops = stats["word_tests"] * OPS_PER_WORD_TEST + stats["ring_evals"] * OPS_PER_RING_EVAL
+    achieved = ops / (ms_per_step / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+            "frac": achieved / alu_peak, "traffic": None,
+            "peak_source": "152 SMs x 128 int32 lanes x max SM clock (recipe unit counts)",
+            "ops_per_step": ops, "counters": stats}
+    in_bytes = sum(x.numel() for x in Xs) + sum(c.numel() for c in Cs if c is not None)
+    alg_bytes = in_bytes + sum(o.numel() for o in outs)
+    gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
+    hbm = {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+           "peak_source": peak_src, "algorithmic_bytes_per_step": alg_bytes}
 
     cpu = None
-    if not args.no_cpu and ws == 1:
+    if not args.no_cpu and ws == 1 and args.workload == "batch512":
         cores = os.cpu_count() or 1
         sample = synth.batch_512(2 * cores, first=10_000)
         rate, cwall, cwork = cpu_oracle_rate(sample, cores)
@@ -276,17 +406,19 @@ def run_hasf(args):
                "sample": f"{len(sample)} images of the workload (other seeds), one oracle "
                          f"process per core, {cwork:.1f} s of CPU work in {cwall:.1f} s"}
 
+    px = sum(x.numel() for x in Xs)
     line = {
-        "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": ws, "steps": args.steps,
+        "metric": metric, "value": value, "unit": "images/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit planes (integer only)",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "images_per_step": BATCH, "width": 512, "height": 512,
-                   "rmax": RMAX, "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+        "config": {"workload": workload, "images_per_step": n,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "l2": "flushed between timed steps (256 MB write, untimed)",
-                   "mpixel_per_s": value * 512 * 512 / 1e6, "wall_s": wall},
-        "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": args.steps, "clocks": clocks,
+                   "mpixel_per_s": px * args.steps * ws / (t_ms / 1e3) / 1e6, "wall_s": wall},
+        "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
+        "gpu_launches": launches,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -301,6 +433,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hasf", choices=["hasf", "reference"])
+    ap.add_argument("--workload", default="batch512", choices=["batch512", "ragged", "large"])
+    ap.add_argument("--ragged-n", type=int, default=1024)
+    ap.add_argument("--side", type=int, default=4096)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -166,9 +166,11 @@ int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
 /* Work counters accumulated by launches made while HASF_OPT_STATS was 1,
  * summed over images: [0] sweep word tests (32-pixel words holding a candidate
  * of the active subfield), [1] shifted feature words read by level updates,
- * [2] subfield passes, [3] priority levels that activated points, [4] rounds.
- * Synchronises the device, copies the first n (1..5) counters to the HOST
- * array out and resets them.  Errors: HASF_EINVAL, HASF_ECUDA. */
+ * [2] subfield passes, [3] priority levels that activated points, [4] rounds,
+ * and [5] the number of kernel launches the context issued since the last
+ * read (counted on the host whatever HASF_OPT_STATS is).  Synchronises the
+ * device, copies the first n (1..6) counters to the HOST array out and resets
+ * them.  Errors: HASF_EINVAL, HASF_ECUDA. */
 int hasf_read_stats(hasf_ctx *ctx, uint64_t *out, int n);
 
 /* Static description of a status code. */

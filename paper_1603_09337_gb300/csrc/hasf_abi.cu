@@ -101,6 +101,7 @@ struct hasf_ctx {
   size_t arena_bytes = 0;
   int* d_status = nullptr;
   unsigned long long* d_stats = nullptr;  // STAT_COUNT counters
+  unsigned long long launches = 0;        // kernel launches issued (host count)
 
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
@@ -297,6 +298,7 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
                    (int)p.reg_order.size(), grid, p.reg_smem,
                    (unsigned*)(base + p.off_counter) + 1, s);
     if (e != cudaSuccess) return cuda_status(e);
+    ++ctx->launches;
   }
   if (!p.order.empty()) {
     const int per_sm = std::max(1, resident_ctas_per_sm(ctx->device, p.smem));
@@ -304,6 +306,7 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
     e = launch_resident(d_jobs, (const int*)(base + p.off_order), (int)p.order.size(), grid,
                         p.smem, (unsigned*)(base + p.off_counter), s);
     if (e != cudaSuccess) return cuda_status(e);
+    ++ctx->launches;
   }
   // Gang jobs: as many as fit co-resident per cooperative launch.
   size_t at = 0;
@@ -317,6 +320,7 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
     }
     e = launch_gang(d_jobs, d_map + at, (int)(end - at), s);
     if (e != cudaSuccess) return cuda_status(e);
+    ++ctx->launches;
     at = end;
   }
   return HASF_OK;
@@ -644,6 +648,17 @@ int hasf_status_of(hasf_ctx* ctx, void* stream) {
   return st == DEV_TIMEOUT ? HASF_ETIMEOUT : (st ? HASF_ECUDA : HASF_OK);
 }
 
+namespace {
+bool is_pinned(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+}  // namespace
+
 int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
   if (!ctx || n < 0 || (n > 0 && !imgs)) return HASF_EINVAL;
   for (int i = 0; i < n; ++i) {
@@ -701,6 +716,9 @@ int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
     }
     char* pin = (char*)ctx->pinned;
     char* dev = (char*)ctx->io;
+    // Pinned caller buffers are copied directly (2D copies honour the pitch);
+    // pageable ones are staged through the context's pinned buffer.
+    std::vector<char> out_pinned(cnt, 0);
     for (int i = 0; i < cnt; ++i) {
       const hasf_image& im = imgs[first + i];
       const size_t w = im.width, h = im.height, px = w * h, ap = align_up(px);
@@ -711,33 +729,41 @@ int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
       di.pitch = im.width;
       di.in = (const uint8_t*)d;
       di.out = (uint8_t*)(d + ap);
+      out_pinned[i] = is_pinned(im.out);
+      const uint8_t* srcs[3] = {im.in, im.C, im.D};
+      const uint8_t** dsts[3] = {&di.in, &di.C, &di.D};
       size_t slot = 2;
-      const uint8_t* srcs[2] = {im.C, im.D};
-      const uint8_t** dsts[2] = {&di.C, &di.D};
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < 3; ++q) {
         if (!srcs[q]) continue;
-        *dsts[q] = (const uint8_t*)(d + ap * slot);
-        for (size_t y = 0; y < h; ++y)
-          std::memcpy(hp + ap * slot + y * w, srcs[q] + y * (size_t)im.pitch, w);
-        ++slot;
+        const size_t at_slot = q == 0 ? 0 : slot++;
+        char* dd = d + ap * at_slot;
+        *dsts[q] = (const uint8_t*)dd;
+        if (is_pinned(srcs[q])) {
+          e = cudaMemcpy2DAsync(dd, w, srcs[q], (size_t)im.pitch, w, h, cudaMemcpyHostToDevice, s);
+        } else {
+          char* hs = hp + ap * at_slot;
+          for (size_t y = 0; y < h; ++y) std::memcpy(hs + y * w, srcs[q] + y * (size_t)im.pitch, w);
+          e = cudaMemcpyAsync(dd, hs, px, cudaMemcpyHostToDevice, s);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
       }
-      for (size_t y = 0; y < h; ++y) std::memcpy(hp + y * w, im.in + y * (size_t)im.pitch, w);
-      e = cudaMemcpyAsync(d, hp, ap, cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess && slot > 2)
-        e = cudaMemcpyAsync(d + 2 * ap, hp + 2 * ap, ap * (slot - 2), cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) return cuda_status(e);
     }
     int rc = run_images(ctx, dimgs.data(), cnt, OP_HASF, s);
     if (rc) return rc;
     for (int i = 0; i < cnt; ++i) {
-      const size_t px = (size_t)imgs[first + i].width * imgs[first + i].height;
-      const size_t ap = align_up(px);
-      e = cudaMemcpyAsync(pin + offs[i] + ap, dev + offs[i] + ap, px, cudaMemcpyDeviceToHost, s);
+      const hasf_image& im = imgs[first + i];
+      const size_t w = im.width, h = im.height, px = w * h, ap = align_up(px);
+      if (out_pinned[i])
+        e = cudaMemcpy2DAsync(im.out, (size_t)im.pitch, dev + offs[i] + ap, w, w, h,
+                              cudaMemcpyDeviceToHost, s);
+      else
+        e = cudaMemcpyAsync(pin + offs[i] + ap, dev + offs[i] + ap, px, cudaMemcpyDeviceToHost, s);
       if (e != cudaSuccess) return cuda_status(e);
     }
     rc = hasf_status_of(ctx, s);
     if (rc) return rc;
     for (int i = 0; i < cnt; ++i) {
+      if (out_pinned[i]) continue;
       const hasf_image& im = imgs[first + i];
       const size_t w = im.width, h = im.height, ap = align_up(w * h);
       for (size_t y = 0; y < h; ++y)
@@ -1000,7 +1026,7 @@ int hasf_tuning_load(hasf_ctx* ctx, const char* path) {
 }
 
 int hasf_read_stats(hasf_ctx* ctx, uint64_t* out, int n) {
-  if (!ctx || !out || n < 1 || n > STAT_COUNT) return HASF_EINVAL;
+  if (!ctx || !out || n < 1 || n > STAT_COUNT + 1) return HASF_EINVAL;
   cudaSetDevice(ctx->device);
   cudaError_t e = cudaDeviceSynchronize();
   unsigned long long buf[STAT_COUNT] = {0};
@@ -1008,7 +1034,9 @@ int hasf_read_stats(hasf_ctx* ctx, uint64_t* out, int n) {
     e = cudaMemcpy(buf, ctx->d_stats, sizeof(buf), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_stats, 0, sizeof(buf));
   if (e != cudaSuccess) return cuda_status(e);
-  for (int i = 0; i < n; ++i) out[i] = buf[i];
+  for (int i = 0; i < n && i < STAT_COUNT; ++i) out[i] = buf[i];
+  if (n > STAT_COUNT) out[STAT_COUNT] = ctx->launches;
+  ctx->launches = 0;
   return HASF_OK;
 }
 
