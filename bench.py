@@ -45,6 +45,23 @@ SM_COUNT = 152
 INT32_LANES_PER_SM = 128
 
 
+def _traffic(workload: str):
+    """DRAM bytes per launch of the headline kernel from its last ncu capture,
+    if the kernel sources are still the ones that capture measured."""
+    import hashlib
+    if workload != "batch512":
+        return None
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "hasf_reg_kernel_traffic.json")))
+        src = b"".join(open(os.path.join(ROOT, "paper_1603_09337_gb300", "csrc", f), "rb").read()
+                       for f in ("hasf_reg.cuh", "hasf_kernels.cu", "hasf_internal.h"))
+        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
+            return None
+        return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    except Exception:
+        return None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -388,7 +405,7 @@ def run_hasf(args):
     ops = stats["word_tests"] * OPS_PER_WORD_TEST + stats["ring_evals"] * OPS_PER_RING_EVAL
     achieved = ops / (ms_per_step / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-            "frac": achieved / alu_peak, "traffic": None,
+            "frac": achieved / alu_peak, "traffic": _traffic(args.workload),
             "peak_source": "152 SMs x 128 int32 lanes x max SM clock (recipe unit counts)",
             "ops_per_step": ops, "counters": stats}
     in_bytes = sum(x.numel() for x in Xs) + sum(c.numel() for c in Cs if c is not None)
