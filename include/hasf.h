@@ -148,9 +148,15 @@ int hasf_drain(hasf_ctx *ctx);
  *   HASF_OPT_SERVE_STREAMS (1..16): concurrent batches of the server;
  *   HASF_OPT_SERVE_BATCH (1..4096): most jobs the server puts in one launch;
  *   HASF_OPT_STATS       (0/1): count the kernels' work (see hasf_read_stats);
- *   HASF_OPT_GENERIC_ONLY (0/1): run images up to 512 x 512 on the generic
- *                        shared-memory kernel instead of the register kernel
- *                        (the result is the same; for comparisons).
+ *   HASF_OPT_GENERIC_ONLY (0/1): run every image on the generic kernels (one
+ *                        CTA with planes in shared memory, or a gang with planes
+ *                        in L2) instead of the register and tiled kernels (the
+ *                        result is the same; for comparisons);
+ *   HASF_OPT_TILES       (0/1/2): images larger than 512 x 512 with rmax <= 31
+ *                        run on the tiled register kernel -- 1 (default): as
+ *                        thread-block clusters when they have at most 16 tiles
+ *                        of 512 x 512, else as a gang; 2: always as a gang;
+ *                        0: never (generic kernels).
  * Errors: HASF_EINVAL for an unknown option or value. */
 enum {
     HASF_OPT_FORCE_GANG = 1,
@@ -159,7 +165,8 @@ enum {
     HASF_OPT_SERVE_STREAMS = 4,
     HASF_OPT_SERVE_BATCH = 5,
     HASF_OPT_STATS = 6,
-    HASF_OPT_GENERIC_ONLY = 7
+    HASF_OPT_GENERIC_ONLY = 7,
+    HASF_OPT_TILES = 8
 };
 int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
 
@@ -191,14 +198,16 @@ int hasf_graph_launch(hasf_graph *graph, void *stream);
 int hasf_graph_destroy(hasf_graph *graph);
 
 /* ---- Autotuner --------------------------------------------------------------
- * Images that do not fit the register kernel run either in the generic
- * shared-memory kernel (one CTA) or in gang mode (several CTAs sharing planes
- * in L2).  hasf_autotune times the candidates -- the one-CTA kernel when the
- * image fits it, and gangs of 1, 2, 4, ... CTAs -- on a synthetic image of
- * the given size, in batches that fill the GPU (throughput, the batched
- * use), and records the fastest for the size bucket (powers of two of width
- * and height, and rmax).  Later batches use the recorded choice.
- * *ctas receives the choice (0 = one-CTA kernel).  Synchronous. */
+ * Images that do not fit the single-tile register kernel can run on the tiled
+ * register kernel (one CTA per 512 x 512 tile), on the generic shared-memory
+ * kernel (one CTA), or on the generic gang (several CTAs sharing planes in L2).
+ * hasf_autotune times these candidates -- tiled when eligible, one-CTA when
+ * the image fits it, and gangs of 1, 2, 4, ... CTAs -- on a synthetic image of
+ * the given size, in batches that fill the GPU (throughput, the batched use),
+ * and records the fastest for the size bucket (powers of two of width and
+ * height, and rmax).  Later batches use the recorded choice.  *ctas receives
+ * it: -1 = tiled, 0 = one-CTA generic, g > 0 = gang of g CTAs (and 0 for
+ * images the single-tile kernel takes).  Synchronous. */
 int hasf_autotune(hasf_ctx *ctx, int32_t width, int32_t height, int32_t rmax,
                   int32_t connectivity, int32_t *ctas);
 /* Save / load the tuned choices as text ("log2w log2h rmax ctas" lines). */

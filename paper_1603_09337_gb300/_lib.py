@@ -19,6 +19,7 @@ HASF_ETIMEOUT, HASF_ECUDA, HASF_ENOTFOUND, HASF_ECANCELLED = 5, 6, 7, 8
 OPT_FORCE_GANG, OPT_GANG_CTAS, OPT_ROUND_CAP, OPT_SERVE_STREAMS, OPT_SERVE_BATCH = 1, 2, 3, 4, 5
 OPT_STATS = 6
 OPT_GENERIC_ONLY = 7
+OPT_TILES = 8
 STAT_NAMES = ("word_tests", "ring_evals", "passes", "levels", "rounds", "launches")
 
 OP_THIN, OP_THICK, OP_HC, OP_HF = 1, 2, 3, 4

@@ -52,6 +52,8 @@ struct Plan {
   std::vector<int> order;       // resident jobs (generic kernel), largest work first
   std::vector<int> reg_order;   // resident jobs (register kernel), largest work first
   size_t reg_smem = 0;          // dynamic shared memory of the register launch
+  std::map<int, std::vector<int>> tile_groups;  // tiles per image -> cluster jobs
+  std::vector<int2> tctamap;    // tiled gang CTAs (job, tile)
   std::vector<int> gang_jobs;   // gang jobs
   std::vector<int2> ctamap;     // gang CTAs (job, part)
   size_t smem = 0;              // dynamic shared memory of the resident launch
@@ -64,9 +66,11 @@ struct Plan {
 
 struct Options {
   int force_gang = 0;
+  int no_tiles = 0;
+  int tile_force = 0;   // 2: send every tiled image to the tiled gang
   int gang_ctas = 0;
   long long round_cap = 0;
-  int serve_streams = 4;
+  int serve_streams = 8;
   int serve_batch = 512;
   int stats = 0;
   int generic_only = 0;
@@ -77,8 +81,9 @@ struct Batch {  // one server launch in flight
   cudaEvent_t done = nullptr;
   void* mem = nullptr;
   size_t bytes = 0;
-  int* h_status = nullptr;  // pinned, one per job
+  int* h_status = nullptr;  // pinned and mapped, one per job: 0 running, 1 + status done
   std::vector<uint64_t> tickets;
+  std::vector<char> reported;
 };
 
 struct Pending {
@@ -95,6 +100,9 @@ struct hasf_ctx {
   int num_sms = 0;
   size_t max_smem = 0;
   int gang_max = 0;
+  int tile_gang_max = 0;
+  std::vector<cudaStream_t> lanes;  // streams for the independent launches of a plan
+  int tile_cluster_ok[17] = {0};  // clusters of n tiles can run (1) or not (0)
   Options opt;
 
   void* arena = nullptr;
@@ -157,11 +165,28 @@ bool fits_resident(const hasf_ctx* ctx, const hasf_image& im) {
   return resident_smem_bytes(im.width, im.height) + 1024 <= ctx->max_smem;
 }
 
+// Path of an image that the register kernel does not take: 1 = tile
+// cluster, 2 = tiled gang, 0 = the generic kernels.
+int tile_path(const hasf_ctx* ctx, const hasf_image& im) {
+  if (ctx->opt.force_gang || ctx->opt.generic_only || ctx->opt.no_tiles) return 0;
+  if (im.rmax > kTileMaxR) return 0;
+  auto it = ctx->tune.find(tune_key(im));
+  if (it != ctx->tune.end() && it->second >= 0) return 0;  // tuned to a generic shape
+  const int nt = tile_count(im.width, im.height);
+  if (ctx->opt.tile_force == 2) return nt <= ctx->tile_gang_max ? 2 : 0;
+  if (nt <= 16 && ctx->tile_cluster_ok[nt]) return 1;
+  if (nt <= ctx->tile_gang_max) return 2;
+  return 0;
+}
+
 bool wants_gang(const hasf_ctx* ctx, const hasf_image& im) {
   if (ctx->opt.force_gang) return true;
   if (!fits_resident(ctx, im)) return true;
   auto it = ctx->tune.find(tune_key(im));
   return it != ctx->tune.end() && it->second > 0 && !reg_kernel_ok(im.width, im.height, im.rmax);
+}
+bool uses_reg(const hasf_ctx* ctx, const hasf_image& im) {
+  return !ctx->opt.force_gang && !ctx->opt.generic_only && reg_kernel_ok(im.width, im.height, im.rmax);
 }
 
 int gang_size(const hasf_ctx* ctx, const hasf_image& im) {
@@ -177,11 +202,13 @@ int gang_size(const hasf_ctx* ctx, const hasf_image& im) {
 // Size (base == nullptr) or fill (base != nullptr) the plan of n images.
 // Returns the scratch bytes.
 size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p, char* base,
-                  int* status_ptr) {
+                  int* status_ptr, int* notify = nullptr) {
   p.jobs.assign(n, Job{});
   p.order.clear();
   p.reg_order.clear();
   p.reg_smem = 0;
+  p.tile_groups.clear();
+  p.tctamap.clear();
   p.gang_jobs.clear();
   p.ctamap.clear();
   p.smem = 0;
@@ -190,12 +217,20 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
   off = align_up(off + sizeof(Job) * (size_t)n);
   p.off_order = off;
   off = align_up(off + sizeof(int) * (size_t)n);
-  // gang CTAs
+  // path of each image: 3 register kernel, 1 tile cluster, 2 tiled gang,
+  // 4 generic gang, 0 generic one-CTA
   int gang_ctas = 0;
-  std::vector<char> is_gang(n, 0);
+  std::vector<char> path(n, 0);
   for (int i = 0; i < n; ++i) {
-    is_gang[i] = wants_gang(ctx, imgs[i]);
-    if (is_gang[i]) gang_ctas += gang_size(ctx, imgs[i]);
+    if (uses_reg(ctx, imgs[i])) {
+      path[i] = 3;
+    } else if (int tp = tile_path(ctx, imgs[i])) {
+      path[i] = (char)tp;
+      if (tp == 2) gang_ctas += tile_count(imgs[i].width, imgs[i].height);
+    } else if (wants_gang(ctx, imgs[i])) {
+      path[i] = 4;
+      gang_ctas += gang_size(ctx, imgs[i]);
+    }
   }
   p.off_ctamap = off;
   off = align_up(off + sizeof(int2) * (size_t)std::max(gang_ctas, 1));
@@ -237,16 +272,25 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
       j.dp = base ? (uint32_t*)(base + off) : nullptr;
       off += align_up(gwords * 4);
     }
-    if (is_gang[i]) {
+    if (path[i] == 4) {
       j.gang = gang_size(ctx, im);
       j.planes = base ? (uint32_t*)(base + off) : nullptr;
       off += align_up(state_bytes(im.width, im.height));
       j.sync = base ? (unsigned*)(base + p.off_sync) + 8 * i : nullptr;
       p.gang_jobs.push_back(i);
-    } else if (!ctx->opt.generic_only && reg_kernel_ok(im.width, im.height, im.rmax)) {
+    } else if (path[i] == 3) {
       j.gang = 1;
       p.reg_order.push_back(i);
       p.reg_smem = std::max(p.reg_smem, reg_kernel_smem(im.width, im.height));
+    } else if (path[i] == 1) {
+      j.gang = tile_count(im.width, im.height);
+      p.tile_groups[j.gang].push_back(i);
+    } else if (path[i] == 2) {
+      j.gang = tile_count(im.width, im.height);
+      j.planes = base ? (uint32_t*)(base + off) : nullptr;
+      off += align_up(tile_gang_words(im.width, im.height) * 4);
+      j.sync = base ? (unsigned*)(base + p.off_sync) + 8 * i : nullptr;
+      for (int t = 0; t < j.gang; ++t) p.tctamap.push_back(make_int2(i, t));
     } else {
       j.gang = 1;
       p.order.push_back(i);
@@ -255,6 +299,8 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
     j.status = status_ptr ? status_ptr
                           : (base ? (int*)(base + p.off_status) + i : nullptr);
     j.stats = ctx->opt.stats ? ctx->d_stats : nullptr;
+    j.sync = base ? (unsigned*)(base + p.off_sync) + 8 * i : nullptr;
+    j.notify = notify ? notify + i : nullptr;
   }
   // Largest work first (the paper's scheduler bound: a worker never holds
   // more than its share of the largest tasks).
@@ -265,6 +311,7 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
   };
   std::stable_sort(p.order.begin(), p.order.end(), by_work);
   std::stable_sort(p.reg_order.begin(), p.reg_order.end(), by_work);
+  for (auto& kv : p.tile_groups) std::stable_sort(kv.second.begin(), kv.second.end(), by_work);
   for (int gi : p.gang_jobs)
     for (int part = 0; part < p.jobs[gi].gang; ++part) p.ctamap.push_back(make_int2(gi, part));
   p.bytes = off;
@@ -272,31 +319,73 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
 }
 
 // Upload the plan's descriptors and launch it on `s`.  `base` is the scratch.
-int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload = true) {
+// Upload the plan's descriptors and launch it on `s`.  When the plan has
+// several independent launches (kernel kinds, cluster sizes, gang chunks) and
+// `fork` is set, they are issued on the context's lane streams after an event
+// on `s`, and `s` waits for all of them: they overlap on the device.
+int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload = true,
+                bool fork = true) {
   const int n = (int)p.jobs.size();
   cudaError_t e = cudaSuccess;
   if (upload) {
-    std::vector<char> head(p.off_ctamap + sizeof(int2) * std::max<size_t>(p.ctamap.size(), 1), 0);
+    std::vector<char> head(
+        p.off_ctamap + sizeof(int2) * std::max<size_t>(p.ctamap.size() + p.tctamap.size(), 1), 0);
     std::memcpy(head.data() + p.off_jobs, p.jobs.data(), sizeof(Job) * n);
     if (!p.order.empty())
       std::memcpy(head.data() + p.off_order, p.order.data(), sizeof(int) * p.order.size());
     if (!p.reg_order.empty())
       std::memcpy(head.data() + p.off_order + sizeof(int) * p.order.size(), p.reg_order.data(),
                   sizeof(int) * p.reg_order.size());
+    size_t at_o = p.order.size() + p.reg_order.size();
+    for (const auto& kv : p.tile_groups) {
+      std::memcpy(head.data() + p.off_order + sizeof(int) * at_o, kv.second.data(),
+                  sizeof(int) * kv.second.size());
+      at_o += kv.second.size();
+    }
     if (!p.ctamap.empty())
       std::memcpy(head.data() + p.off_ctamap, p.ctamap.data(), sizeof(int2) * p.ctamap.size());
+    if (!p.tctamap.empty())
+      std::memcpy(head.data() + p.off_ctamap + sizeof(int2) * p.ctamap.size(), p.tctamap.data(),
+                  sizeof(int2) * p.tctamap.size());
     e = cudaMemcpyAsync(base, head.data(), head.size(), cudaMemcpyHostToDevice, s);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(base + p.off_counter, 0, 16, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(base + p.off_sync, 0, p.sync_bytes, s);
   if (e != cudaSuccess) return cuda_status(e);
   const Job* d_jobs = (const Job*)(base + p.off_jobs);
+  const int groups = (p.reg_order.empty() ? 0 : 1) + (p.order.empty() ? 0 : 1) +
+                     (int)p.tile_groups.size() + (p.tctamap.empty() ? 0 : 1) +
+                     (p.ctamap.empty() ? 0 : 1);
+  const int nl = (fork && groups > 1) ? std::min<int>(groups, (int)ctx->lanes.size()) : 0;
+  cudaEvent_t ev_fork = nullptr;
+  if (nl > 0) {
+    e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_fork, s);
+    for (int l = 0; e == cudaSuccess && l < nl; ++l) e = cudaStreamWaitEvent(ctx->lanes[l], ev_fork, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  int next_lane = 0;
+  auto lane = [&]() -> cudaStream_t { return nl > 0 ? ctx->lanes[(next_lane++) % nl] : s; };
+  auto join = [&]() -> int {
+    if (nl == 0) return HASF_OK;
+    cudaError_t ej = cudaSuccess;
+    for (int l = 0; ej == cudaSuccess && l < nl; ++l) {
+      cudaEvent_t ev;
+      ej = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (ej != cudaSuccess) break;
+      ej = cudaEventRecord(ev, ctx->lanes[l]);
+      if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, ev, 0);
+      cudaEventDestroy(ev);
+    }
+    cudaEventDestroy(ev_fork);
+    return cuda_status(ej);
+  };
   if (!p.reg_order.empty()) {
     const int per_sm = std::max(1, reg_ctas_per_sm(p.reg_smem));
     const int grid = std::min<int>((int)p.reg_order.size(), per_sm * ctx->num_sms);
     e = launch_reg(d_jobs, (const int*)(base + p.off_order) + p.order.size(),
                    (int)p.reg_order.size(), grid, p.reg_smem,
-                   (unsigned*)(base + p.off_counter) + 1, s);
+                   (unsigned*)(base + p.off_counter) + 1, lane());
     if (e != cudaSuccess) return cuda_status(e);
     ++ctx->launches;
   }
@@ -304,13 +393,44 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
     const int per_sm = std::max(1, resident_ctas_per_sm(ctx->device, p.smem));
     const int grid = std::min<int>((int)p.order.size(), per_sm * ctx->num_sms);
     e = launch_resident(d_jobs, (const int*)(base + p.off_order), (int)p.order.size(), grid,
-                        p.smem, (unsigned*)(base + p.off_counter), s);
+                        p.smem, (unsigned*)(base + p.off_counter), lane());
     if (e != cudaSuccess) return cuda_status(e);
     ++ctx->launches;
+  }
+  // Tile clusters: one launch per cluster size.
+  {
+    size_t at_o = p.order.size() + p.reg_order.size();
+    for (const auto& kv : p.tile_groups) {
+      e = launch_tile_cluster(d_jobs, (const int*)(base + p.off_order) + at_o,
+                              (int)kv.second.size(), kv.first, lane());
+      if (e != cudaSuccess) return cuda_status(e);
+      ++ctx->launches;
+      at_o += kv.second.size();
+    }
+  }
+  // Tiled gangs: as many whole images as fit co-resident per cooperative launch
+  // (the chunks of one kind run one after the other on one stream).
+  if (!p.tctamap.empty()) {
+    const cudaStream_t ls = lane();
+    const int2* d_tmap = (const int2*)(base + p.off_ctamap) + p.ctamap.size();
+    size_t at = 0;
+    while (at < p.tctamap.size()) {
+      size_t end = at;
+      while (end < p.tctamap.size()) {
+        const int gsz = p.jobs[p.tctamap[end].x].gang;
+        if (end > at && (int)(end - at) + gsz > ctx->tile_gang_max) break;
+        end += gsz;
+      }
+      e = launch_tile_gang(d_jobs, d_tmap + at, (int)(end - at), ls);
+      if (e != cudaSuccess) return cuda_status(e);
+      ++ctx->launches;
+      at = end;
+    }
   }
   // Gang jobs: as many as fit co-resident per cooperative launch.
   size_t at = 0;
   const int2* d_map = (const int2*)(base + p.off_ctamap);
+  const cudaStream_t gs = p.ctamap.empty() ? s : lane();
   while (at < p.ctamap.size()) {
     size_t end = at;
     while (end < p.ctamap.size()) {
@@ -318,12 +438,12 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
       if (end > at && (int)(end - at) + gsz > ctx->gang_max) break;
       end += gsz;
     }
-    e = launch_gang(d_jobs, d_map + at, (int)(end - at), s);
+    e = launch_gang(d_jobs, d_map + at, (int)(end - at), gs);
     if (e != cudaSuccess) return cuda_status(e);
     ++ctx->launches;
     at = end;
   }
-  return HASF_OK;
+  return join();
 }
 
 int ensure_arena(hasf_ctx* ctx, size_t bytes, cudaStream_t s) {
@@ -402,13 +522,27 @@ size_t serve_job_bytes(hasf_ctx* ctx, const hasf_image& im) {
 void retire_finished(hasf_ctx* ctx) {  // ctx->mu held
   for (size_t i = 0; i < ctx->inflight.size();) {
     Batch& b = ctx->inflight[i];
+    // jobs report themselves as they finish (their CTAs write the mapped flags)
+    for (size_t k = 0; k < b.tickets.size(); ++k) {
+      if (b.reported[k]) continue;
+      const int f = *(volatile int*)(b.h_status + k);
+      if (f) {
+        b.reported[k] = 1;
+        const int st = f - 1;
+        ctx->finished[b.tickets[k]] = st == DEV_TIMEOUT ? HASF_ETIMEOUT : st;
+        ctx->launched.erase(b.tickets[k]);
+        ctx->cv.notify_all();
+      }
+    }
     cudaError_t q = cudaEventQuery(b.done);
     if (q == cudaErrorNotReady) {
       ++i;
       continue;
     }
     for (size_t k = 0; k < b.tickets.size(); ++k) {
-      int st = q == cudaSuccess ? b.h_status[k] : HASF_ECUDA;
+      if (b.reported[k]) continue;
+      const int f = *(volatile int*)(b.h_status + k);
+      const int st = (q == cudaSuccess && f) ? f - 1 : HASF_ECUDA;
       ctx->finished[b.tickets[k]] = st == DEV_TIMEOUT ? HASF_ETIMEOUT : st;
       ctx->launched.erase(b.tickets[k]);
     }
@@ -423,20 +557,28 @@ void retire_finished(hasf_ctx* ctx) {  // ctx->mu held
   }
 }
 
-// Admit pending jobs (FIFO) that fit the budget into one batch and launch it.
+// Admit pending jobs that fit the budget into one batch and launch it.  A
+// batch holds jobs of one kind -- images the single-tile kernel takes, or
+// larger ones -- taken in arrival order starting from the oldest job, so that
+// short jobs never wait in a launch for a long one.
 bool launch_next(hasf_ctx* ctx) {  // ctx->mu held
   if (ctx->pending.empty() || ctx->free_streams.empty()) return false;
   std::vector<hasf_image> imgs;
   std::vector<uint64_t> tickets;
   size_t bytes = 0;
-  while (!ctx->pending.empty() && (int)imgs.size() < ctx->opt.serve_batch) {
-    const Pending& pj = ctx->pending.front();
-    if (ctx->inflight_bytes + bytes + pj.bytes + 65536 > ctx->budget) break;
-    imgs.push_back(pj.img);
-    tickets.push_back(pj.ticket);
-    bytes += pj.bytes;
-    ctx->queued.erase(pj.ticket);
-    ctx->pending.pop_front();
+  const bool small = uses_reg(ctx, ctx->pending.front().img);
+  for (auto it = ctx->pending.begin();
+       it != ctx->pending.end() && (int)imgs.size() < ctx->opt.serve_batch;) {
+    if (uses_reg(ctx, it->img) != small) {
+      ++it;
+      continue;
+    }
+    if (ctx->inflight_bytes + bytes + it->bytes + 65536 > ctx->budget) break;
+    imgs.push_back(it->img);
+    tickets.push_back(it->ticket);
+    bytes += it->bytes;
+    ctx->queued.erase(it->ticket);
+    it = ctx->pending.erase(it);
   }
   if (imgs.empty()) return false;
   Batch b;
@@ -447,17 +589,20 @@ bool launch_next(hasf_ctx* ctx) {  // ctx->mu held
   const int n = (int)imgs.size();
   b.bytes = build_plan(ctx, imgs.data(), n, OP_HASF, p, nullptr, nullptr);
   cudaError_t e = cudaMallocAsync(&b.mem, b.bytes, b.stream);
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.h_status, sizeof(int) * n, 0);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.h_status, sizeof(int) * n, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
+  int* d_notify = nullptr;
+  if (e == cudaSuccess) {
+    std::memset(b.h_status, 0, sizeof(int) * n);
+    e = cudaHostGetDevicePointer((void**)&d_notify, b.h_status, 0);
+  }
+  b.reported.assign(n, 0);
   int rc = cuda_status(e);
   if (rc == HASF_OK) {
-    build_plan(ctx, imgs.data(), n, OP_HASF, p, (char*)b.mem, nullptr);
+    build_plan(ctx, imgs.data(), n, OP_HASF, p, (char*)b.mem, nullptr, d_notify);
     e = cudaMemsetAsync((char*)b.mem + p.off_status, 0, sizeof(int) * n, b.stream);
     rc = cuda_status(e);
-    if (rc == HASF_OK) rc = launch_plan(ctx, p, (char*)b.mem, b.stream);
-    if (rc == HASF_OK)
-      rc = cuda_status(cudaMemcpyAsync(b.h_status, (char*)b.mem + p.off_status, sizeof(int) * n,
-                                       cudaMemcpyDeviceToHost, b.stream));
+    if (rc == HASF_OK) rc = launch_plan(ctx, p, (char*)b.mem, b.stream, true, false);
     if (rc == HASF_OK) rc = cuda_status(cudaEventRecord(b.done, b.stream));
   }
   if (rc != HASF_OK) {
@@ -545,6 +690,13 @@ int hasf_create(hasf_ctx** out, int device, size_t mem_budget_bytes) {
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   c->max_smem = max_resident_smem(device);
   c->gang_max = std::max(1, max_gang_ctas(device));
+  c->tile_gang_max = max_tile_gang_ctas(device);
+  for (int l = 0; l < 8; ++l) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) c->lanes.push_back(st);
+    else cudaGetLastError();
+  }
+  for (int t = 1; t <= 16; ++t) c->tile_cluster_ok[t] = tile_clusters_possible(t) > 0 ? 1 : 0;
   e = cudaMalloc(&c->d_status, 16);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, 16);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_stats, sizeof(unsigned long long) * STAT_COUNT);
@@ -573,6 +725,7 @@ int hasf_destroy(hasf_ctx* ctx) {
   }
   if (ctx->worker_running) ctx->worker.join();
   for (cudaStream_t st : ctx->free_streams) cudaStreamDestroy(st);
+  for (cudaStream_t st : ctx->lanes) cudaStreamDestroy(st);
   cudaDeviceSynchronize();
   if (ctx->arena) cudaFree(ctx->arena);
   if (ctx->io) cudaFree(ctx->io);
@@ -615,6 +768,11 @@ int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
     case HASF_OPT_GENERIC_ONLY:
       if (value != 0 && value != 1) return HASF_EINVAL;
       ctx->opt.generic_only = (int)value;
+      return HASF_OK;
+    case HASF_OPT_TILES:
+      if (value < 0 || value > 2) return HASF_EINVAL;
+      ctx->opt.no_tiles = value == 0;
+      ctx->opt.tile_force = (int)value == 2 ? 2 : 0;
       return HASF_OK;
     default:
       return HASF_EINVAL;
@@ -950,7 +1108,14 @@ int hasf_autotune(hasf_ctx* ctx, int32_t width, int32_t height, int32_t rmax, in
   }
   for (int c = 0; c < copies_max; ++c)
     cudaMemcpy(dev + px * 2 * c, host.data(), px, cudaMemcpyHostToDevice);
+  // candidates: -1 = tiled register kernel, 0 = generic one-CTA kernel,
+  // g > 0 = generic gang of g CTAs
   std::vector<int> cands;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->tune.erase(tune_key(im));
+  }
+  if (tile_path(ctx, im)) cands.push_back(-1);
   if (fits_resident(ctx, im)) cands.push_back(0);
   for (int g = 1; g <= ctx->gang_max; g *= 2) cands.push_back(g);
   const Options saved = ctx->opt;
@@ -962,16 +1127,21 @@ int hasf_autotune(hasf_ctx* ctx, int32_t width, int32_t height, int32_t rmax, in
   int best_c = cands.empty() ? 1 : cands.back();
   int rc = HASF_OK;
   for (int c : cands) {
-    const int per = c == 0 ? std::max(1, 2 * ctx->num_sms) : std::max(1, ctx->gang_max / c);
+    const int nt = tile_count(width, height);
+    const int per = c < 0 ? std::max(1, ctx->num_sms / std::max(1, nt))
+                          : (c == 0 ? std::max(1, 2 * ctx->num_sms) : std::max(1, ctx->gang_max / c));
     const int copies = std::min(copies_max, per);
     std::vector<hasf_image> batch(copies, im);
     for (int k = 0; k < copies; ++k) {
       batch[k].in = dev + px * 2 * k;
       batch[k].out = dev + px * 2 * k + px;
     }
-    ctx->opt.force_gang = c > 0;
-    ctx->opt.gang_ctas = c;
-    ctx->opt.generic_only = 1;
+    ctx->opt = saved;
+    if (c >= 0) {
+      ctx->opt.force_gang = c > 0;
+      ctx->opt.gang_ctas = c;
+      ctx->opt.generic_only = 1;
+    }
     rc = run_images(ctx, batch.data(), copies, OP_HASF, s);  // warm-up
     if (rc == HASF_OK) rc = hasf_status_of(ctx, s);
     if (rc != HASF_OK) break;

@@ -48,6 +48,7 @@ struct Job {
   unsigned* sync;    // gang mode: 8 barrier words; else null
   int* status;       // device status word of the job
   unsigned long long* stats;  // work counters (see StatIndex) or null
+  int* notify;       // host-mapped word set to 1 + status when the job is done, or null
   int w, h, pitch, wpr;
   int r_lo, r_hi;
   int op;
@@ -88,6 +89,15 @@ bool reg_kernel_ok(int w, int h, int rmax);
 int reg_ctas_per_sm(size_t smem_bytes);
 cudaError_t launch_reg(const Job* d_jobs, const int* d_order, int njobs, int grid,
                        size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
+size_t tile_kernel_smem();
+int tile_count(int w, int h);
+size_t tile_gang_words(int w, int h);
+int tile_clusters_possible(int csize);
+cudaError_t launch_tile_cluster(const Job* d_jobs, const int* d_order, int njobs, int csize,
+                                cudaStream_t s);
+int max_tile_gang_ctas(int device);
+cudaError_t launch_tile_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);
+constexpr int kTileMaxR = 31;   // the tiled kernels take rmax <= 31
 int max_gang_ctas(int device);
 size_t max_resident_smem(int device);
 int resident_ctas_per_sm(int device, size_t smem_bytes);

@@ -463,6 +463,23 @@ __device__ bool run_hf(Ctx<Mode>& k, const Job& jb, int r) {
   return run_operator<Mode, CONN>(k, r, true, nullptr, jb.g0);
 }
 
+// End of a job on one of its CTAs: the last of the job's CTAs to get here
+// publishes the job's status to the host (1 + status), after a system-scope
+// fence that orders the job's output writes before it.
+__device__ __forceinline__ void job_done(const Job& jb, int gang) {
+  if (!jb.notify) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence_system();
+    const unsigned c = atomicAdd(jb.sync + 3, 1u);
+    if (c + 1u == (unsigned)gang) {
+      const int st = atomicAdd(jb.status, 0);
+      __threadfence_system();
+      *(volatile int*)jb.notify = 1 + st;
+    }
+  }
+}
+
 template <class Mode, int CONN>
 __device__ void run_job(Ctx<Mode>& k, const Job& jb, uint32_t* planes_base) {
   load_job(k, jb, planes_base);
@@ -485,6 +502,7 @@ __device__ void run_job(Ctx<Mode>& k, const Job& jb, uint32_t* planes_base) {
   } else if (threadIdx.x == 0) {
     atomicMax(jb.status, (int)DEV_TIMEOUT);
   }
+  job_done(jb, jb.gang);
   if (jb.stats) {
     unsigned long long t = k.n_tests, r = k.n_ring;
     for (int o = 16; o > 0; o >>= 1) {
@@ -575,6 +593,7 @@ hasf_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) 
 }  // namespace hasf
 
 #include "hasf_reg.cuh"
+#include "hasf_tiled.cuh"
 
 namespace hasf {
 
@@ -738,6 +757,81 @@ cudaError_t launch_reg(const Job* d_jobs, const int* d_order, int njobs, int gri
   if (e != cudaSuccess) return e;
   hasf_reg_kernel<<<grid, kThreads, smem_bytes, s>>>(d_jobs, d_order, njobs, d_counter);
   return cudaGetLastError();
+}
+
+size_t tile_kernel_smem() { return tile_smem_bytes(); }
+int tile_count(int w, int h) { return tiles_x(w) * tiles_y(h); }
+size_t tile_gang_words(int w, int h) { return (size_t)tile_count(w, h) * kGangTileWords; }
+
+// Clusters of csize CTAs of the tile kernel that can run at once (0: none).
+int tile_clusters_possible(int csize) {
+  if (csize < 1 || csize > 16) return 0;
+  const size_t smem = tile_smem_bytes();
+  cudaFuncSetAttribute(hasf_tile_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  cudaFuncSetAttribute(hasf_tile_cluster_kernel,
+                       cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(csize);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = csize;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, hasf_tile_cluster_kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+cudaError_t launch_tile_cluster(const Job* d_jobs, const int* d_order, int njobs, int csize,
+                                cudaStream_t s) {
+  const size_t smem = tile_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(hasf_tile_cluster_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(hasf_tile_cluster_kernel,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(njobs * csize);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = csize;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, hasf_tile_cluster_kernel, d_jobs, d_order);
+}
+
+int max_tile_gang_ctas(int device) {
+  int per_sm = 0, sms = 0;
+  const size_t smem = tile_smem_bytes();
+  cudaFuncSetAttribute(hasf_tile_gang_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hasf_tile_gang_kernel, kThreads, smem);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return per_sm * sms;
+}
+
+cudaError_t launch_tile_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s) {
+  const size_t smem = tile_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(hasf_tile_gang_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  void* args[] = {(void*)&d_jobs, (void*)&d_ctamap};
+  return cudaLaunchCooperativeKernel((const void*)hasf_tile_gang_kernel, dim3(nctas),
+                                     dim3(kThreads), args, smem, s);
 }
 
 cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, int grid,

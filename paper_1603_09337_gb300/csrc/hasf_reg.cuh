@@ -386,6 +386,7 @@ __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
   } else if (threadIdx.x == 0) {
     atomicMax(jb.status, (int)DEV_TIMEOUT);
   }
+  job_done(jb, 1);
   if (jb.stats) {
     unsigned long long t = g.n_tests, rr = g.n_ring;
     for (int o = 16; o > 0; o >>= 1) {

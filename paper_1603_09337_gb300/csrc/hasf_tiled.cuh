@@ -1,0 +1,601 @@
+// hasf_tiled.cuh -- register-resident HASF for images larger than one tile
+// (included by hasf_kernels.cu after hasf_reg.cuh, whose helpers it uses).
+//
+// The image is cut into tiles of 512 x 512 pixels (16 words x 512 rows), one
+// CTA per tile, each running the register scheme of the single-tile kernel:
+// thread (warp w, lane l) owns word column l & 15 of a 16-row strip.  Tiles
+// exchange what crosses their borders:
+//   - after every half-round (all rows of one parity updated), their first and
+//     last word columns, the candidates of their first column, and their first
+//     and last rows; each tile then copies its neighbours' into halo arrays
+//     (left/right columns with the corner words, the rows above and below);
+//   - at the start of every operator, the 31 rows and the word column around
+//     the tile of the priority snapshot F, for the ring reads of the level
+//     updates (the kernel takes rmax <= 31).
+// Inside a fused half-round the rightmost word's odd pixel 31 needs its right
+// neighbour's even pixel 0 as updated by the neighbour's own even-column pass;
+// that one bit is computed here again from the halo (the neighbour computes the
+// same bit from the same data), so a half-round needs no extra barrier.
+// Global OR-reductions (level activated anything, round changed anything) and
+// barriers go through an exchange policy: a thread-block cluster (shared
+// memory of the other CTAs, hardware cluster barrier) for images of up to 16
+// tiles, or global memory and a bounded gang barrier for larger images.
+#pragma once
+
+#include <cooperative_groups.h>
+
+namespace hasf {
+
+namespace cg = cooperative_groups;
+
+constexpr int kTW = 16;                  // words per tile row
+constexpr int kTH = kRegRows;            // rows per tile (512)
+constexpr int kTPad = kRegPadR;          // F halo rows (31)
+constexpr int kFP = kTW + 3;             // F row pitch: words -1..16, one pad (odd)
+constexpr int kFR = kTH + 2 * kTPad;     // F rows: -31 .. 542
+constexpr int kTileF = ((kFR * kFP + 2) + 3) & ~3;
+// published boundary (same layout in shared or global memory)
+constexpr int kPubCol0 = 0, kPubCol15 = kTH, kPubCand0 = 2 * kTH, kPubTop = 3 * kTH,
+              kPubBot = 3 * kTH + kTW, kPubWords = 3 * kTH + 2 * kTW;
+// fetched halo
+constexpr int kHLcol = 0, kHRcol = kTH + 2, kHRcand = 2 * (kTH + 2), kHAbove = kHRcand + kTH,
+              kHBelow = kHAbove + kTW + 2, kHaloWords = kHBelow + kTW + 2;
+// the published area is double-buffered: a tile rewrites a buffer only after
+// every tile has passed the barrier that follows its last read of it
+constexpr int kTileSmemWords = kTileF + 2 * kRegPlane + kRegXchg + 2 * kPubWords + kHaloWords + 8;
+
+__host__ __device__ inline int tiles_x(int w) { return (words_per_row(w) + kTW - 1) / kTW; }
+__host__ __device__ inline int tiles_y(int h) { return (h + kTH - 1) / kTH; }
+inline size_t tile_smem_bytes() { return (size_t)kTileSmemWords * 4; }
+// global words per tile of the gang policy: published boundary (two buffers) + F centre
+constexpr int kGangTileWords = 2 * kPubWords + kTH * kTW;
+
+// ---------------------------------------------------------------------------
+// Exchange policies.
+// ---------------------------------------------------------------------------
+
+struct ClusterX {
+  uint32_t* pub;   // this CTA's published boundary (shared memory)
+  uint32_t* Fc;    // this CTA's F plane at (row 0, word 0)
+  int* flags;      // two OR slots (shared memory)
+  int slot;
+  int* bcast;
+  int ntx, nty, tx, ty;
+  __device__ __forceinline__ bool has(int x, int y) const {
+    return x >= 0 && x < ntx && y >= 0 && y < nty;
+  }
+  __device__ __forceinline__ int rank_of(int x, int y) const { return y * ntx + x; }
+  __device__ __forceinline__ uint32_t pub_ld(int x, int y, int off) const {
+    return *cg::this_cluster().map_shared_rank(pub + off, rank_of(x, y));
+  }
+  __device__ __forceinline__ uint32_t f_ld(int x, int y, int row, int word) const {
+    return *cg::this_cluster().map_shared_rank(Fc + row * kFP + word, rank_of(x, y));
+  }
+  __device__ __forceinline__ void pub_st(int off, uint32_t v) { pub[off] = v; }
+  __device__ __forceinline__ void f_publish(int, int, uint32_t) {}  // F is read in place
+  __device__ __forceinline__ void sync() { cg::this_cluster().sync(); }
+  __device__ int sync_or(int v) {
+    const int local = __syncthreads_or(v);
+    if (threadIdx.x == 0) flags[slot] = local;
+    cg::this_cluster().sync();
+    if (threadIdx.x == 0) {
+      int any = 0;
+      const int n = ntx * nty;
+      for (int r = 0; r < n; ++r) any |= *cg::this_cluster().map_shared_rank(flags + slot, r);
+      *bcast = any;
+    }
+    __syncthreads();
+    slot ^= 1;
+    return *bcast;
+  }
+  __device__ __forceinline__ bool failed() const { return false; }
+};
+
+struct GangX {
+  uint32_t* gbase;  // kGangTileWords per tile of this image, row-major tiles
+  GangMode gm;
+  int ntx, nty, tx, ty;
+  __device__ __forceinline__ bool has(int x, int y) const {
+    return x >= 0 && x < ntx && y >= 0 && y < nty;
+  }
+  __device__ __forceinline__ uint32_t* tile(int x, int y) const {
+    return gbase + (size_t)(y * ntx + x) * kGangTileWords;
+  }
+  __device__ __forceinline__ uint32_t pub_ld(int x, int y, int off) const {
+    return __ldcg(tile(x, y) + off);
+  }
+  __device__ __forceinline__ uint32_t f_ld(int x, int y, int row, int word) const {
+    return __ldcg(tile(x, y) + 2 * kPubWords + row * kTW + word);
+  }
+  __device__ __forceinline__ void pub_st(int off, uint32_t v) { __stcg(tile(tx, ty) + off, v); }
+  __device__ __forceinline__ void f_publish(int row, int word, uint32_t v) {
+    __stcg(tile(tx, ty) + 2 * kPubWords + row * kTW + word, v);
+  }
+  __device__ __forceinline__ void sync() { gm.barrier(0); }
+  __device__ __forceinline__ int sync_or(int v) { return gm.barrier(v); }
+  __device__ __forceinline__ bool failed() const { return gm.failed(); }
+};
+
+template <class X>
+struct TileCtx {
+  X x;
+  Ctx<SmemMode> g;   // image geometry and counters; g.F = F plane at (row 0, word 0)
+  uint32_t* M;       // 512 x kRegPitch
+  uint32_t* cand;    // 512 x kRegPitch
+  uint32_t* xtop;    // [warp][16] first row of each warp of this tile
+  uint32_t* xbot;    // [warp][16] last row of each warp
+  uint32_t* halo;
+  int warp, half, j, s0;
+  int pb;            // published-area buffer of the next publish (0 or 1)
+  int x0w, y0;       // first word and row of the tile in the image
+  bool jin;          // this thread's word lies inside the image
+  __device__ __forceinline__ bool row_in(int R) const { return y0 + R < g.h; }
+};
+
+// Write this tile's boundary for its neighbours: columns 0 and 15, the
+// candidates of column 0, rows 0 and 511.
+// Every publish is followed by one barrier and one tile_fetch.
+template <class X>
+__device__ __forceinline__ void tile_publish(TileCtx<X>& k, const uint32_t (&S)[kRegR]) {
+  const int b = k.pb * kPubWords;
+  if (k.j == 0 || k.j == kTW - 1) {
+    const int off = b + (k.j == 0 ? kPubCol0 : kPubCol15);
+#pragma unroll
+    for (int q = 0; q < kRegR; ++q) k.x.pub_st(off + k.s0 + q, S[q]);
+    if (k.j == 0)
+#pragma unroll
+      for (int q = 0; q < kRegR; ++q)
+        k.x.pub_st(b + kPubCand0 + k.s0 + q, k.cand[(k.s0 + q) * kRegPitch]);
+  }
+  if (k.warp == 0 && k.half == 0) k.x.pub_st(b + kPubTop + k.j, S[0]);
+  if (k.warp == (int)(blockDim.x >> 5) - 1 && k.half == 1)
+    k.x.pub_st(b + kPubBot + k.j, S[kRegR - 1]);
+}
+
+// Copy the neighbours' published boundaries (the buffer of the last publish)
+// into the halo arrays, then switch buffers.
+template <class X>
+__device__ void tile_fetch(TileCtx<X>& k) {
+  uint32_t* h = k.halo;
+  const int tx = k.x.tx, ty = k.x.ty;
+  const int b = k.pb * kPubWords;
+  k.pb ^= 1;
+  for (int i = threadIdx.x; i < kTH + 2; i += blockDim.x) {
+    const int R = i - 1;
+    const int dy = R < 0 ? -1 : (R >= kTH ? 1 : 0);
+    const int rr = R - dy * kTH;
+    h[kHLcol + i] =
+        k.x.has(tx - 1, ty + dy) ? k.x.pub_ld(tx - 1, ty + dy, b + kPubCol15 + rr) : 0u;
+    h[kHRcol + i] =
+        k.x.has(tx + 1, ty + dy) ? k.x.pub_ld(tx + 1, ty + dy, b + kPubCol0 + rr) : 0u;
+    if (R >= 0 && R < kTH)
+      h[kHRcand + R] = k.x.has(tx + 1, ty) ? k.x.pub_ld(tx + 1, ty, b + kPubCand0 + R) : 0u;
+  }
+  for (int i = threadIdx.x; i < kTW; i += blockDim.x) {
+    h[kHAbove + 1 + i] = k.x.has(tx, ty - 1) ? k.x.pub_ld(tx, ty - 1, b + kPubBot + i) : 0u;
+    h[kHBelow + 1 + i] = k.x.has(tx, ty + 1) ? k.x.pub_ld(tx, ty + 1, b + kPubTop + i) : 0u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    h[kHAbove] = h[kHLcol + 0];
+    h[kHAbove + kTW + 1] = h[kHRcol + 0];
+    h[kHBelow] = h[kHLcol + kTH + 1];
+    h[kHBelow + kTW + 1] = h[kHRcol + kTH + 1];
+  }
+  __syncthreads();
+}
+
+// The two subfield passes (0, SY), (1, SY) over this thread's rows of parity SY,
+// fused row by row as in the single-tile kernel, with the tile's left/right
+// neighbour words from the halo and the right neighbour's even pixel 0
+// recomputed for the odd pass.
+template <int CONN, int SY, class X>
+__device__ __forceinline__ uint32_t tile_half(TileCtx<X>& k, uint32_t (&S)[kRegR], bool thin,
+                                              uint32_t above, uint32_t below) {
+  const int j = k.j;
+  const uint32_t* lcol = k.halo + kHLcol;   // index = tile row + 1
+  const uint32_t* rcol = k.halo + kHRcol;
+  const uint32_t* rcand = k.halo + kHRcand;
+  uint32_t* cr = k.cand + k.s0 * kRegPitch + j;
+  uint32_t changed = 0;
+#pragma unroll
+  for (int r = SY; r < kRegR; r += 2) {
+    uint32_t cw = cr[r * kRegPitch];
+    const int R = k.s0 + r;
+    const bool redge = j == kTW - 1 && (rcand[R] & 1u);
+    if (!__any_sync(0xFFFFFFFFu, cw != 0u || redge)) continue;
+    const uint32_t n = r > 0 ? S[r - 1] : above;
+    uint32_t c = S[r];
+    const uint32_t s = r + 1 < kRegR ? S[r + 1] : below;
+    uint32_t nw = __shfl_up_sync(0xFFFFFFFFu, n, 1, 16);
+    uint32_t wv = __shfl_up_sync(0xFFFFFFFFu, c, 1, 16);
+    uint32_t sw = __shfl_up_sync(0xFFFFFFFFu, s, 1, 16);
+    uint32_t ne = __shfl_down_sync(0xFFFFFFFFu, n, 1, 16);
+    uint32_t e = __shfl_down_sync(0xFFFFFFFFu, c, 1, 16);
+    uint32_t se = __shfl_down_sync(0xFFFFFFFFu, s, 1, 16);
+    if (j == 0) {
+      nw = lcol[R];
+      wv = lcol[R + 1];
+      sw = lcol[R + 2];
+    }
+    if (j == kTW - 1) {
+      ne = rcol[R];
+      e = rcol[R + 1];
+      se = rcol[R + 2];
+    }
+    uint32_t sm = simple_bits<CONN>(nw, n, ne, wv, c, e, sw, s, se);
+    const uint32_t chg0 = cw & 0x55555555u & sm;
+    // the right neighbour's pixel 0 after its even-column pass: its 3 x 3
+    // words are (n, ne, -), (c, e, -), (s, se, -) seen from its side
+    uint32_t e1 = e;
+    if (redge) {
+      const uint32_t smr = simple_bits<CONN>(n, ne, 0u, c, e, 0u, s, se, 0u);
+      const uint32_t cr0 = rcand[R] & 1u & smr;
+      e1 = thin ? (e & ~cr0) : (e | cr0);
+    }
+    if (__any_sync(0xFFFFFFFFu, chg0 != 0u || e1 != e)) {
+      c = thin ? (c & ~chg0) : (c | chg0);
+      cw &= ~chg0;
+      wv = __shfl_up_sync(0xFFFFFFFFu, c, 1, 16);
+      uint32_t e2 = __shfl_down_sync(0xFFFFFFFFu, c, 1, 16);
+      if (j == 0) wv = lcol[R + 1];
+      if (j == kTW - 1) e2 = e1;
+      sm = simple_bits<CONN>(nw, n, ne, wv, c, e2, sw, s, se);
+    }
+    const uint32_t chg1 = cw & 0xAAAAAAAAu & sm;
+    c = thin ? (c & ~chg1) : (c | chg1);
+    cw &= ~chg1;
+    const uint32_t chg = chg0 | chg1;
+    if (chg) {
+      S[r] = c;
+      cr[r * kRegPitch] = cw;
+      changed |= chg;
+    }
+  }
+  return changed;
+}
+
+// Row above / below this thread's strip at its column: the other strip of the
+// warp, the neighbouring warp, or the tile above / below (halo).
+template <class X>
+__device__ __forceinline__ uint32_t tile_above(TileCtx<X>& k, const uint32_t (&S)[kRegR]) {
+  const int lane = threadIdx.x & 31;
+  uint32_t v = __shfl_sync(0xFFFFFFFFu, S[kRegR - 1], lane ^ 16);
+  if (k.half == 0)
+    v = k.warp > 0 ? k.xbot[(k.warp - 1) * kTW + k.j] : k.halo[kHAbove + 1 + k.j];
+  return v;
+}
+template <class X>
+__device__ __forceinline__ uint32_t tile_below(TileCtx<X>& k, const uint32_t (&S)[kRegR]) {
+  const int lane = threadIdx.x & 31;
+  uint32_t v = __shfl_sync(0xFFFFFFFFu, S[0], lane ^ 16);
+  if (k.half == 1)
+    v = (k.warp + 1) < (int)(blockDim.x >> 5) ? k.xtop[(k.warp + 1) * kTW + k.j]
+                                             : k.halo[kHBelow + 1 + k.j];
+  return v;
+}
+
+template <int CONN, class X>
+__device__ bool tile_level(TileCtx<X>& k, uint32_t (&S)[kRegR], bool thin) {
+  for (int round = 0;; ++round) {
+    if (round >= k.g.cap) return false;
+    ++k.g.n_rounds;
+    k.g.n_passes += 4;
+    k.g.n_tests += 2 * kRegR;
+    uint32_t ch = tile_half<CONN, 0>(k, S, thin, tile_above(k, S), 0u);
+    if (k.half == 0) k.xtop[k.warp * kTW + k.j] = S[0];
+    tile_publish(k, S);
+    k.x.sync();
+    if (k.x.failed()) return false;
+    tile_fetch(k);
+    ch |= tile_half<CONN, 1>(k, S, thin, 0u, tile_below(k, S));
+    if (k.half == 1) k.xbot[k.warp * kTW + k.j] = S[kRegR - 1];
+    tile_publish(k, S);
+    const int any = k.x.sync_or(ch != 0u);
+    if (k.x.failed()) return false;
+    tile_fetch(k);
+    if (!any) return true;
+  }
+}
+
+template <int CONN, class X>
+__device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r, bool thin,
+                              const uint32_t* pos, const uint32_t* neg) {
+  Ctx<SmemMode>& g = k.g;
+  uint32_t pendrows = 0;
+  // snapshot F (centre), movable mask, no candidates
+#pragma unroll
+  for (int q = 0; q < kRegR; ++q) {
+    const int R = k.s0 + q;
+    uint32_t m = 0;
+    if (k.row_in(R) && k.jin) {
+      const int t = (k.y0 + R) * g.wpr + k.x0w + k.j;
+      m = g.rowmask(k.x0w + k.j);
+      if (pos) m &= pos[t];
+      if (neg) m &= ~neg[t];
+      if (m & (thin ? S[q] : ~S[q])) pendrows |= 1u << q;
+    }
+    g.F[R * kFP + k.j] = S[q];
+    k.x.f_publish(R, k.j, S[q]);
+    k.M[R * kRegPitch + k.j] = m;
+    k.cand[R * kRegPitch + k.j] = 0u;
+  }
+  if (k.half == 0) k.xtop[k.warp * kTW + k.j] = S[0];
+  if (k.half == 1) k.xbot[k.warp * kTW + k.j] = S[kRegR - 1];
+  tile_publish(k, S);
+  k.x.sync();
+  if (k.x.failed()) return false;
+  // F halo: 31 rows above and below (words -1..16), words -1 and 16 beside
+  {
+    const int tx = k.x.tx, ty = k.x.ty;
+    const int band = kTPad * (kTW + 2);
+    for (int i = threadIdx.x; i < 2 * band + 2 * kTH; i += blockDim.x) {
+      int R, w;
+      if (i < 2 * band) {
+        const int b = i < band ? i : i - band;
+        R = i < band ? -kTPad + b / (kTW + 2) : kTH + b / (kTW + 2);
+        w = b % (kTW + 2) - 1;
+      } else {
+        const int b = i - 2 * band;
+        R = b % kTH;
+        w = b < kTH ? -1 : kTW;
+      }
+      const int dx = w < 0 ? -1 : (w >= kTW ? 1 : 0);
+      const int dy = R < 0 ? -1 : (R >= kTH ? 1 : 0);
+      const uint32_t v = k.x.has(tx + dx, ty + dy)
+                             ? k.x.f_ld(tx + dx, ty + dy, R - dy * kTH, w - dx * kTW)
+                             : 0u;
+      g.F[R * kFP + w] = v;
+    }
+  }
+  tile_fetch(k);   // includes __syncthreads
+  const int nlev = c_lv.nlev[r];
+  for (int li = 0; li < nlev; ++li) {
+    const int o0 = c_lv.start[li], o1 = c_lv.start[li + 1];
+    uint32_t newrows = 0;
+#pragma unroll
+    for (int g4 = 0; g4 < kRegR; g4 += 4) {
+      if (!((pendrows >> g4) & 0xFu)) continue;
+      uint32_t pend[4], acc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = g4 + u;
+        pend[u] = 0u;
+        if ((pendrows >> q) & 1u) {
+          const int a = (k.s0 + q) * kRegPitch + k.j;
+          pend[u] = k.M[a] & (thin ? S[q] : ~S[q]) & ~k.cand[a];
+          if (!pend[u]) pendrows &= ~(1u << q);
+        }
+        acc[u] = thin ? 0xFFFFFFFFu : 0u;
+      }
+      if (!(pend[0] | pend[1] | pend[2] | pend[3])) continue;
+      const uint32_t* base = g.F + (k.s0 + g4) * kFP + k.j;
+      for (int o = o0; o < o1; ++o) {
+        const int dx = c_lv.off[o][0], dy = c_lv.off[o][1];
+        const uint32_t* p0 = base + dy * kFP + (dx >> 5);
+        const int sh = dx & 31;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (pend[u]) {
+            const uint32_t v = __funnelshift_r(p0[u * kFP], p0[u * kFP + 1], sh);
+            acc[u] = thin ? (acc[u] & v) : (acc[u] | v);
+          }
+        }
+        ++g.n_ring;
+        if (((o - o0) & 3) == 3) {
+          uint32_t left = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) left |= pend[u] & (thin ? acc[u] : ~acc[u]);
+          if (!left) break;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t add = pend[u] & (thin ? ~acc[u] : acc[u]);
+        if (add) {
+          const int q = g4 + u;
+          k.cand[(k.s0 + q) * kRegPitch + k.j] |= add;
+          newrows |= 1u << q;
+          if (!(pend[u] & ~add)) pendrows &= ~(1u << q);
+        }
+      }
+    }
+    __syncthreads();
+    tile_publish(k, S);   // column-0 candidates changed
+    const int any = k.x.sync_or(newrows != 0u);
+    if (k.x.failed()) return false;
+    tile_fetch(k);
+    if (!any) continue;
+    ++g.n_levels;
+    if (!tile_level<CONN>(k, S, thin)) return false;
+  }
+  return true;
+}
+
+template <int CONN, class X>
+__device__ void tile_job(TileCtx<X>& k, const Job& jb, uint32_t* smem) {
+  Ctx<SmemMode>& g = k.g;
+  uint32_t S[kRegR];
+  for (int t = threadIdx.x; t < kTileSmemWords; t += blockDim.x) smem[t] = 0u;
+  {
+    const bool vec = ((reinterpret_cast<uintptr_t>(jb.in) | (uintptr_t)jb.pitch |
+                       reinterpret_cast<uintptr_t>(jb.C) | reinterpret_cast<uintptr_t>(jb.D)) &
+                      15u) == 0;
+    const bool cx = jb.op == OP_HASF || jb.op == OP_HC;
+    const int wimg = k.x0w + k.j;
+#pragma unroll
+    for (int q = 0; q < kRegR; ++q) {
+      const int R = k.s0 + q;
+      uint32_t xs = 0;
+      if (k.row_in(R) && k.jin) {
+        const size_t off = (size_t)(k.y0 + R) * jb.pitch + (wimg << 5);
+        const int n = min(32, g.w - (wimg << 5));
+        xs = pack_word(jb.in + off, n, vec);
+        const int t = (k.y0 + R) * g.wpr + wimg;
+        if (jb.cp) {
+          const uint32_t cs = jb.C ? pack_word(jb.C + off, n, vec) : 0u;
+          jb.cp[t] = cx ? (cs & xs) : cs;
+        }
+        if (jb.dp) jb.dp[t] = (jb.D ? pack_word(jb.D + off, n, vec) : 0u) & ~xs;
+      }
+      S[q] = xs;
+    }
+    __syncthreads();
+  }
+  auto snapshot_g0 = [&]() {
+#pragma unroll
+    for (int q = 0; q < kRegR; ++q) {
+      const int R = k.s0 + q;
+      if (k.row_in(R) && k.jin) jb.g0[(k.y0 + R) * g.wpr + k.x0w + k.j] = S[q];
+    }
+    __syncthreads();
+  };
+  bool ok = true;
+  auto hc = [&](int r) {
+    snapshot_g0();
+    if (!tile_operator<CONN>(k, S, r, true, nullptr, jb.cp)) return false;
+    return tile_operator<CONN>(k, S, r, false, jb.g0, nullptr);
+  };
+  auto hf = [&](int r) {
+    snapshot_g0();
+    if (!tile_operator<CONN>(k, S, r, false, nullptr, jb.dp)) return false;
+    return tile_operator<CONN>(k, S, r, true, nullptr, jb.g0);
+  };
+  switch (jb.op) {
+    case OP_HASF:
+      for (int r = jb.r_lo; ok && r <= jb.r_hi; ++r) {
+        ok = hc(r);
+        if (ok) ok = hf(r);
+      }
+      break;
+    case OP_THIN: ok = tile_operator<CONN>(k, S, jb.r_hi, true, nullptr, jb.cp); break;
+    case OP_THICK: ok = tile_operator<CONN>(k, S, jb.r_hi, false, jb.cp, nullptr); break;
+    case OP_HC: ok = hc(jb.r_hi); break;
+    case OP_HF: ok = hf(jb.r_hi); break;
+    default: ok = false;
+  }
+  if (ok) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(jb.out) | (uintptr_t)jb.pitch) & 15u) == 0;
+    const int wimg = k.x0w + k.j;
+#pragma unroll
+    for (int q = 0; q < kRegR; ++q) {
+      const int R = k.s0 + q;
+      if (!k.row_in(R) || !k.jin) continue;
+      const uint32_t v = S[q];
+      uint8_t* o = jb.out + (size_t)(k.y0 + R) * jb.pitch + (wimg << 5);
+      const int n = min(32, g.w - (wimg << 5));
+      if (vec && n == 32) {
+        uint32_t wds[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const uint32_t nib = (v >> (4 * e)) & 0xFu;
+          wds[e] = (nib & 1u) | ((nib & 2u) << 7) | ((nib & 4u) << 14) | ((nib & 8u) << 21);
+        }
+        reinterpret_cast<uint4*>(o)[0] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+        reinterpret_cast<uint4*>(o)[1] = make_uint4(wds[4], wds[5], wds[6], wds[7]);
+      } else {
+        for (int b = 0; b < n; ++b) o[b] = (uint8_t)((v >> b) & 1u);
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicMax(jb.status, (int)DEV_TIMEOUT);
+  }
+  job_done(jb, k.x.ntx * k.x.nty);
+  if (jb.stats) {
+    unsigned long long t = g.n_tests, rr = g.n_ring;
+    for (int o = 16; o > 0; o >>= 1) {
+      t += __shfl_down_sync(0xFFFFFFFFu, t, o);
+      rr += __shfl_down_sync(0xFFFFFFFFu, rr, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(jb.stats + STAT_WORD_TESTS, t);
+      atomicAdd(jb.stats + STAT_RING_EVALS, rr);
+    }
+    if (threadIdx.x == 0 && k.x.tx == 0 && k.x.ty == 0) {
+      atomicAdd(jb.stats + STAT_PASSES, (unsigned long long)g.n_passes);
+      atomicAdd(jb.stats + STAT_LEVELS, (unsigned long long)g.n_levels);
+      atomicAdd(jb.stats + STAT_ROUNDS, (unsigned long long)g.n_rounds);
+    }
+  }
+}
+
+template <class X>
+__device__ __forceinline__ void tile_init(TileCtx<X>& k, const Job& jb, uint32_t* smem, int tx,
+                                          int ty) {
+  Ctx<SmemMode>& g = k.g;
+  g.w = jb.w;
+  g.h = jb.h;
+  g.wpr = jb.wpr;
+  g.P = kFP;
+  const int rem = jb.w & 31;
+  g.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
+  g.S = nullptr;
+  g.cand = nullptr;
+  g.F = smem + 1 + kTPad * kFP + 1;   // row 0, word 0 (word -1 is one to the left)
+  g.cap = jb.cap;
+  g.n_tests = g.n_ring = g.n_passes = g.n_levels = g.n_rounds = 0;
+  k.M = smem + kTileF;
+  k.cand = k.M + kRegPlane;
+  k.xtop = k.cand + kRegPlane;
+  k.xbot = k.xtop + (kThreads / 32) * kTW;
+  k.halo = k.xbot + (kThreads / 32) * kTW + 2 * kPubWords;   // published area, then halo
+  k.pb = 0;
+  k.warp = threadIdx.x >> 5;
+  k.half = (threadIdx.x >> 4) & 1;
+  k.j = threadIdx.x & 15;
+  k.s0 = (2 * k.warp + k.half) * kRegR;
+  k.x0w = tx * kTW;
+  k.y0 = ty * kTH;
+  k.jin = k.x0w + k.j < jb.wpr;
+  k.x.ntx = tiles_x(jb.w);
+  k.x.nty = tiles_y(jb.h);
+  k.x.tx = tx;
+  k.x.ty = ty;
+}
+
+// One cluster of ntx * nty CTAs per image: cluster i works on job order[i].
+__global__ void __launch_bounds__(kThreads, 1)
+hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ order) {
+  extern __shared__ uint4 smem4[];
+  uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
+  __shared__ int flags[2], bcast;
+  cg::cluster_group cl = cg::this_cluster();
+  const int csize = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const Job& jb = jobs[order[blockIdx.x / csize]];
+  const int ntx = tiles_x(jb.w);
+  TileCtx<ClusterX> k;
+  tile_init(k, jb, smem, rank % ntx, rank / ntx);
+  k.x.pub = k.xbot + (kThreads / 32) * kTW;
+  k.x.Fc = k.g.F;
+  k.x.flags = flags;
+  k.x.slot = 0;
+  k.x.bcast = &bcast;
+  if (threadIdx.x == 0) flags[0] = flags[1] = 0;
+  cl.sync();
+  if (jb.conn == 4) tile_job<4>(k, jb, smem);
+  else tile_job<8>(k, jb, smem);
+  cl.sync();   // no CTA leaves while others may still read its shared memory
+}
+
+// Gang mode with tiles: CTA b works on tile ctamap[b].y of job ctamap[b].x.
+__global__ void __launch_bounds__(kThreads, 1)
+hasf_tile_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) {
+  extern __shared__ uint4 smem4[];
+  uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
+  __shared__ int flag;
+  const int2 m = ctamap[blockIdx.x];
+  const Job& jb = jobs[m.x];
+  const int ntx = tiles_x(jb.w);
+  TileCtx<GangX> k;
+  tile_init(k, jb, smem, m.y % ntx, m.y / ntx);
+  k.x.gbase = jb.planes;
+  k.x.gm.sync_words = jb.sync;
+  k.x.gm.nctas = jb.gang;
+  k.x.gm.flag_smem = &flag;
+  k.x.gm.dead = 0;
+  if (jb.conn == 4) tile_job<4>(k, jb, smem);
+  else tile_job<8>(k, jb, smem);
+}
+
+}  // namespace hasf
