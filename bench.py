@@ -344,8 +344,16 @@ def run_hasf(args):
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    graph = ctx.graph_create(imgs) if args.graph else None
+
+    def step():
+        if graph is not None:
+            ctx.graph_launch(graph)
+        else:
+            ctx.smooth_batch_raw(arr, n)
+
     for _ in range(args.warmup):
-        ctx.smooth_batch_raw(arr, n)
+        step()
     ctx.status()
     stats = ctx.stats_step(arr, n)          # work counters of one step (untimed run)
 
@@ -358,12 +366,15 @@ def run_hasf(args):
         for i in range(args.steps):
             flush.zero_()                       # evict L2 (129 MB) between steps, untimed
             starts[i].record(stream)
-            ctx.smooth_batch_raw(arr, n)
+            step()
             ends[i].record(stream)
         barrier()
         wall = time.perf_counter() - wall0
     ctx.status()
     launches = ctx.read_stats()["launches"]   # kernel launches inside the timed region
+    if graph is not None:
+        launches = stats["launches"] * args.steps  # the graph holds one step's launches
+        ctx.graph_destroy(graph)
     t_ms = replicas.max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), dev)
     value = n * args.steps * ws / (t_ms / 1e3)
     ms_per_step = t_ms / args.steps
@@ -432,6 +443,7 @@ def run_hasf(args):
         "config": {"workload": workload, "images_per_step": n,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                    "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "launch": "CUDA graph replay" if args.graph else "hasf_smooth_batch",
                    "mpixel_per_s": px * args.steps * ws / (t_ms / 1e3) / 1e6, "wall_s": wall},
         "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
         "gpu_launches": launches,
@@ -454,6 +466,7 @@ def main():
     ap.add_argument("--ragged-n", type=int, default=1024)
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
