@@ -5,9 +5,9 @@
 // CTA per tile, each running the register scheme of the single-tile kernel:
 // thread (warp w, lane l) owns word column l & 15 of a 16-row strip.  Tiles
 // exchange what crosses their borders:
-//   - after every half-round (all rows of one parity updated), their first and
-//     last word columns, the candidates of their first column, and their first
-//     and last rows; each tile then copies its neighbours' into halo arrays
+//   - after every half-round (all rows of one parity updated) and every level
+//     update, their first and last word columns, the candidates of their first
+//     column, and their first and last rows, into the neighbours' halo arrays
 //     (left/right columns with the corner words, the rows above and below);
 //   - at the start of every operator, the 31 rows and the word column around
 //     the tile of the priority snapshot F, for the ring reads of the level
@@ -16,10 +16,13 @@
 // neighbour's even pixel 0 as updated by the neighbour's own even-column pass;
 // that one bit is computed here again from the halo (the neighbour computes the
 // same bit from the same data), so a half-round needs no extra barrier.
-// Global OR-reductions (level activated anything, round changed anything) and
-// barriers go through an exchange policy: a thread-block cluster (shared
-// memory of the other CTAs, hardware cluster barrier) for images of up to 16
-// tiles, or global memory and a bounded gang barrier for larger images.
+// An exchange moves the boundaries, ORs one flag over all tiles (level
+// activated anything, round changed anything) and is one barrier.  Two
+// policies: a thread-block cluster for images of up to 16 tiles, where each
+// tile stores its boundary straight into its neighbours' shared memory before
+// the hardware cluster barrier; or, for larger images, a gang that publishes
+// boundaries to global memory, meets at a bounded gang barrier and then reads
+// its neighbours'.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -34,15 +37,21 @@ constexpr int kTPad = kRegPadR;          // F halo rows (31)
 constexpr int kFP = kTW + 3;             // F row pitch: words -1..16, one pad (odd)
 constexpr int kFR = kTH + 2 * kTPad;     // F rows: -31 .. 542
 constexpr int kTileF = ((kFR * kFP + 2) + 3) & ~3;
-// published boundary (same layout in shared or global memory)
+// boundary published to global memory by the gang policy (double-buffered)
 constexpr int kPubCol0 = 0, kPubCol15 = kTH, kPubCand0 = 2 * kTH, kPubTop = 3 * kTH,
               kPubBot = 3 * kTH + kTW, kPubWords = 3 * kTH + 2 * kTW;
-// fetched halo
-constexpr int kHLcol = 0, kHRcol = kTH + 2, kHRcand = 2 * (kTH + 2), kHAbove = kHRcand + kTH,
-              kHBelow = kHAbove + kTW + 2, kHaloWords = kHBelow + kTW + 2;
-// the published area is double-buffered: a tile rewrites a buffer only after
-// every tile has passed the barrier that follows its last read of it
-constexpr int kTileSmemWords = kTileF + 2 * kRegPlane + kRegXchg + 2 * kPubWords + kHaloWords + 8;
+// halo array: left / right neighbour column at rows -1..512 (index row + 1),
+// right neighbour's column-0 candidates, rows above and below.  A strip's 16
+// rows start on a 16-byte boundary, so they move as four 16-byte stores.
+constexpr int kHLcol = 3, kHRcol = kHLcol + kTH + 4, kHRcand = kHRcol + kTH + 5,
+              kHAbove = kHRcand + kTH, kHBelow = kHAbove + kTW, kHaloWords = kHBelow + kTW;
+static_assert((kHLcol + 1) % 4 == 0 && (kHRcol + 1) % 4 == 0 && kHRcand % 4 == 0 &&
+                  kHaloWords % 4 == 0,
+              "halo strips must be 16-byte aligned");
+// Both policies double-buffer the halo: exchange n fills buffer n & 1; every
+// read of a buffer happens between the barriers of exchanges n and n + 1, and
+// the next write to it comes after the barrier of exchange n + 1.
+constexpr int kTileSmemWords = kTileF + 2 * kRegPlane + kRegXchg + 2 * kHaloWords + 8;
 
 __host__ __device__ inline int tiles_x(int w) { return (words_per_row(w) + kTW - 1) / kTW; }
 __host__ __device__ inline int tiles_y(int h) { return (h + kTH - 1) / kTH; }
@@ -55,39 +64,22 @@ constexpr int kGangTileWords = 2 * kPubWords + kTH * kTW;
 // ---------------------------------------------------------------------------
 
 struct ClusterX {
-  uint32_t* pub;   // this CTA's published boundary (shared memory)
-  uint32_t* Fc;    // this CTA's F plane at (row 0, word 0)
-  int* flags;      // two OR slots (shared memory)
+  uint32_t* halo2;  // this CTA's two halo buffers; the same offset in every CTA
+  uint32_t* Fc;     // this CTA's F plane at (row 0, word 0)
+  int* flags;       // three OR slots (shared memory), exchange n uses slot n % 3
   int slot;
-  int* bcast;
   int ntx, nty, tx, ty;
   __device__ __forceinline__ bool has(int x, int y) const {
     return x >= 0 && x < ntx && y >= 0 && y < nty;
   }
   __device__ __forceinline__ int rank_of(int x, int y) const { return y * ntx + x; }
-  __device__ __forceinline__ uint32_t pub_ld(int x, int y, int off) const {
-    return *cg::this_cluster().map_shared_rank(pub + off, rank_of(x, y));
+  __device__ __forceinline__ uint32_t* remote(int dx, int dy, int idx) const {
+    return cg::this_cluster().map_shared_rank(halo2 + idx, rank_of(tx + dx, ty + dy));
   }
   __device__ __forceinline__ uint32_t f_ld(int x, int y, int row, int word) const {
     return *cg::this_cluster().map_shared_rank(Fc + row * kFP + word, rank_of(x, y));
   }
-  __device__ __forceinline__ void pub_st(int off, uint32_t v) { pub[off] = v; }
   __device__ __forceinline__ void f_publish(int, int, uint32_t) {}  // F is read in place
-  __device__ __forceinline__ void sync() { cg::this_cluster().sync(); }
-  __device__ int sync_or(int v) {
-    const int local = __syncthreads_or(v);
-    if (threadIdx.x == 0) flags[slot] = local;
-    cg::this_cluster().sync();
-    if (threadIdx.x == 0) {
-      int any = 0;
-      const int n = ntx * nty;
-      for (int r = 0; r < n; ++r) any |= *cg::this_cluster().map_shared_rank(flags + slot, r);
-      *bcast = any;
-    }
-    __syncthreads();
-    slot ^= 1;
-    return *bcast;
-  }
   __device__ __forceinline__ bool failed() const { return false; }
 };
 
@@ -111,8 +103,6 @@ struct GangX {
   __device__ __forceinline__ void f_publish(int row, int word, uint32_t v) {
     __stcg(tile(tx, ty) + 2 * kPubWords + row * kTW + word, v);
   }
-  __device__ __forceinline__ void sync() { gm.barrier(0); }
-  __device__ __forceinline__ int sync_or(int v) { return gm.barrier(v); }
   __device__ __forceinline__ bool failed() const { return gm.failed(); }
 };
 
@@ -124,19 +114,18 @@ struct TileCtx {
   uint32_t* cand;    // 512 x kRegPitch
   uint32_t* xtop;    // [warp][16] first row of each warp of this tile
   uint32_t* xbot;    // [warp][16] last row of each warp
-  uint32_t* halo;
+  uint32_t* halo2;   // two halo buffers of kHaloWords
+  uint32_t* halo;    // the buffer filled by the last exchange
   int warp, half, j, s0;
-  int pb;            // published-area buffer of the next publish (0 or 1)
+  int pb;            // buffer of the next exchange (0 or 1)
   int x0w, y0;       // first word and row of the tile in the image
   bool jin;          // this thread's word lies inside the image
   __device__ __forceinline__ bool row_in(int R) const { return y0 + R < g.h; }
 };
 
-// Write this tile's boundary for its neighbours: columns 0 and 15, the
-// candidates of column 0, rows 0 and 511.
-// Every publish is followed by one barrier and one tile_fetch.
-template <class X>
-__device__ __forceinline__ void tile_publish(TileCtx<X>& k, const uint32_t (&S)[kRegR]) {
+// Gang policy: write this tile's boundary (columns 0 and 15, the candidates
+// of column 0, rows 0 and 511) to its published area pb in global memory.
+__device__ __forceinline__ void gang_publish(TileCtx<GangX>& k, const uint32_t (&S)[kRegR]) {
   const int b = k.pb * kPubWords;
   if (k.j == 0 || k.j == kTW - 1) {
     const int off = b + (k.j == 0 ? kPubCol0 : kPubCol15);
@@ -152,14 +141,11 @@ __device__ __forceinline__ void tile_publish(TileCtx<X>& k, const uint32_t (&S)[
     k.x.pub_st(b + kPubBot + k.j, S[kRegR - 1]);
 }
 
-// Copy the neighbours' published boundaries (the buffer of the last publish)
-// into the halo arrays, then switch buffers.
-template <class X>
-__device__ void tile_fetch(TileCtx<X>& k) {
-  uint32_t* h = k.halo;
+// Gang policy: copy the neighbours' published area pb into halo buffer pb.
+__device__ void gang_fetch(TileCtx<GangX>& k) {
+  uint32_t* h = k.halo2 + k.pb * kHaloWords;
   const int tx = k.x.tx, ty = k.x.ty;
   const int b = k.pb * kPubWords;
-  k.pb ^= 1;
   for (int i = threadIdx.x; i < kTH + 2; i += blockDim.x) {
     const int R = i - 1;
     const int dy = R < 0 ? -1 : (R >= kTH ? 1 : 0);
@@ -172,17 +158,76 @@ __device__ void tile_fetch(TileCtx<X>& k) {
       h[kHRcand + R] = k.x.has(tx + 1, ty) ? k.x.pub_ld(tx + 1, ty, b + kPubCand0 + R) : 0u;
   }
   for (int i = threadIdx.x; i < kTW; i += blockDim.x) {
-    h[kHAbove + 1 + i] = k.x.has(tx, ty - 1) ? k.x.pub_ld(tx, ty - 1, b + kPubBot + i) : 0u;
-    h[kHBelow + 1 + i] = k.x.has(tx, ty + 1) ? k.x.pub_ld(tx, ty + 1, b + kPubTop + i) : 0u;
+    h[kHAbove + i] = k.x.has(tx, ty - 1) ? k.x.pub_ld(tx, ty - 1, b + kPubBot + i) : 0u;
+    h[kHBelow + i] = k.x.has(tx, ty + 1) ? k.x.pub_ld(tx, ty + 1, b + kPubTop + i) : 0u;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    h[kHAbove] = h[kHLcol + 0];
-    h[kHAbove + kTW + 1] = h[kHRcol + 0];
-    h[kHBelow] = h[kHLcol + kTH + 1];
-    h[kHBelow + kTW + 1] = h[kHRcol + kTH + 1];
+}
+
+// One exchange: every tile's boundary into its neighbours' halo buffer pb and
+// the OR of v over all threads of all tiles, at the cost of one barrier.
+// Gang policy: publish, gang barrier (which carries the OR), read.
+__device__ int tile_exchange(TileCtx<GangX>& k, const uint32_t (&S)[kRegR], int v) {
+  gang_publish(k, S);
+  const int any = k.x.gm.barrier(v);
+  if (k.x.failed()) return 0;
+  gang_fetch(k);
+  k.halo = k.halo2 + k.pb * kHaloWords;
+  k.pb ^= 1;
+  return any;
+}
+
+__device__ __forceinline__ void st4(uint32_t* d, uint32_t a, uint32_t b, uint32_t c,
+                                    uint32_t e) {
+  *reinterpret_cast<uint4*>(d) = make_uint4(a, b, c, e);
+}
+
+// Cluster policy: stores into the neighbours' shared memory, OR flags, one
+// hardware cluster barrier (release / acquire: the stores are visible after it).
+__device__ int tile_exchange(TileCtx<ClusterX>& k, const uint32_t (&S)[kRegR], int v) {
+  const ClusterX& x = k.x;
+  const int o = k.pb * kHaloWords;
+  const int tx = x.tx, ty = x.ty;
+  const bool top = k.s0 == 0, bot = k.s0 + kRegR == kTH;
+  if (k.j == 0 && x.has(tx - 1, ty)) {
+    // left neighbour: its right column and its right column's candidates
+    uint32_t* d = x.remote(-1, 0, o + kHRcol + 1 + k.s0);
+#pragma unroll
+    for (int q = 0; q < kRegR; q += 4) st4(d + q, S[q], S[q + 1], S[q + 2], S[q + 3]);
+    const uint32_t* c = k.cand + k.s0 * kRegPitch;
+    uint32_t* e = x.remote(-1, 0, o + kHRcand + k.s0);
+#pragma unroll
+    for (int q = 0; q < kRegR; q += 4)
+      st4(e + q, c[q * kRegPitch], c[(q + 1) * kRegPitch], c[(q + 2) * kRegPitch],
+          c[(q + 3) * kRegPitch]);
   }
-  __syncthreads();
+  if (k.j == kTW - 1 && x.has(tx + 1, ty)) {
+    uint32_t* d = x.remote(1, 0, o + kHLcol + 1 + k.s0);
+#pragma unroll
+    for (int q = 0; q < kRegR; q += 4) st4(d + q, S[q], S[q + 1], S[q + 2], S[q + 3]);
+  }
+  // corner words (row 0 or 511 of column 0 or 15) for the diagonal tiles
+  if (k.j == 0 && top && x.has(tx - 1, ty - 1)) *x.remote(-1, -1, o + kHRcol + kTH + 1) = S[0];
+  if (k.j == 0 && bot && x.has(tx - 1, ty + 1)) *x.remote(-1, 1, o + kHRcol) = S[kRegR - 1];
+  if (k.j == kTW - 1 && top && x.has(tx + 1, ty - 1))
+    *x.remote(1, -1, o + kHLcol + kTH + 1) = S[0];
+  if (k.j == kTW - 1 && bot && x.has(tx + 1, ty + 1)) *x.remote(1, 1, o + kHLcol) = S[kRegR - 1];
+  if (top && x.has(tx, ty - 1)) *x.remote(0, -1, o + kHBelow + k.j) = S[0];
+  if (bot && x.has(tx, ty + 1)) *x.remote(0, 1, o + kHAbove + k.j) = S[kRegR - 1];
+  // OR flag: every warp that saw v sets slot n % 3 in every tile (all write the
+  // same value, so plain stores do); each tile clears the slot of exchange
+  // n + 2, whose last reads came before this barrier and whose next writes
+  // come after the next one.
+  const int lane = threadIdx.x & 31;
+  if (__any_sync(0xFFFFFFFFu, v) && lane < x.ntx * x.nty)
+    *cg::this_cluster().map_shared_rank(x.flags + x.slot, lane) = 1;
+  cg::this_cluster().sync();
+  const int any = *(volatile int*)(x.flags + x.slot);
+  if (threadIdx.x == 0) x.flags[x.slot == 0 ? 2 : x.slot - 1] = 0;
+  k.x.slot = x.slot == 2 ? 0 : x.slot + 1;
+  k.halo = k.halo2 + o;
+  k.pb ^= 1;
+  return any;
 }
 
 // The two subfield passes (0, SY), (1, SY) over this thread's rows of parity SY,
@@ -262,7 +307,7 @@ __device__ __forceinline__ uint32_t tile_above(TileCtx<X>& k, const uint32_t (&S
   const int lane = threadIdx.x & 31;
   uint32_t v = __shfl_sync(0xFFFFFFFFu, S[kRegR - 1], lane ^ 16);
   if (k.half == 0)
-    v = k.warp > 0 ? k.xbot[(k.warp - 1) * kTW + k.j] : k.halo[kHAbove + 1 + k.j];
+    v = k.warp > 0 ? k.xbot[(k.warp - 1) * kTW + k.j] : k.halo[kHAbove + k.j];
   return v;
 }
 template <class X>
@@ -271,7 +316,7 @@ __device__ __forceinline__ uint32_t tile_below(TileCtx<X>& k, const uint32_t (&S
   uint32_t v = __shfl_sync(0xFFFFFFFFu, S[0], lane ^ 16);
   if (k.half == 1)
     v = (k.warp + 1) < (int)(blockDim.x >> 5) ? k.xtop[(k.warp + 1) * kTW + k.j]
-                                             : k.halo[kHBelow + 1 + k.j];
+                                             : k.halo[kHBelow + k.j];
   return v;
 }
 
@@ -284,16 +329,12 @@ __device__ bool tile_level(TileCtx<X>& k, uint32_t (&S)[kRegR], bool thin) {
     k.g.n_tests += 2 * kRegR;
     uint32_t ch = tile_half<CONN, 0>(k, S, thin, tile_above(k, S), 0u);
     if (k.half == 0) k.xtop[k.warp * kTW + k.j] = S[0];
-    tile_publish(k, S);
-    k.x.sync();
+    tile_exchange(k, S, 0);
     if (k.x.failed()) return false;
-    tile_fetch(k);
     ch |= tile_half<CONN, 1>(k, S, thin, 0u, tile_below(k, S));
     if (k.half == 1) k.xbot[k.warp * kTW + k.j] = S[kRegR - 1];
-    tile_publish(k, S);
-    const int any = k.x.sync_or(ch != 0u);
+    const int any = tile_exchange(k, S, ch != 0u);
     if (k.x.failed()) return false;
-    tile_fetch(k);
     if (!any) return true;
   }
 }
@@ -322,8 +363,7 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r, bool t
   }
   if (k.half == 0) k.xtop[k.warp * kTW + k.j] = S[0];
   if (k.half == 1) k.xbot[k.warp * kTW + k.j] = S[kRegR - 1];
-  tile_publish(k, S);
-  k.x.sync();
+  tile_exchange(k, S, 0);
   if (k.x.failed()) return false;
   // F halo: 31 rows above and below (words -1..16), words -1 and 16 beside
   {
@@ -348,7 +388,7 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r, bool t
       g.F[R * kFP + w] = v;
     }
   }
-  tile_fetch(k);   // includes __syncthreads
+  __syncthreads();
   const int nlev = c_lv.nlev[r];
   for (int li = 0; li < nlev; ++li) {
     const int o0 = c_lv.start[li], o1 = c_lv.start[li + 1];
@@ -400,11 +440,8 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r, bool t
         }
       }
     }
-    __syncthreads();
-    tile_publish(k, S);   // column-0 candidates changed
-    const int any = k.x.sync_or(newrows != 0u);
+    const int any = tile_exchange(k, S, newrows != 0u);   // column-0 candidates changed
     if (k.x.failed()) return false;
-    tile_fetch(k);
     if (!any) continue;
     ++g.n_levels;
     if (!tile_level<CONN>(k, S, thin)) return false;
@@ -413,10 +450,9 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r, bool t
 }
 
 template <int CONN, class X>
-__device__ void tile_job(TileCtx<X>& k, const Job& jb, uint32_t* smem) {
+__device__ __forceinline__ void tile_job(TileCtx<X>& k, const Job& jb, uint32_t* smem) {
   Ctx<SmemMode>& g = k.g;
   uint32_t S[kRegR];
-  for (int t = threadIdx.x; t < kTileSmemWords; t += blockDim.x) smem[t] = 0u;
   {
     const bool vec = ((reinterpret_cast<uintptr_t>(jb.in) | (uintptr_t)jb.pitch |
                        reinterpret_cast<uintptr_t>(jb.C) | reinterpret_cast<uintptr_t>(jb.D)) &
@@ -538,7 +574,8 @@ __device__ __forceinline__ void tile_init(TileCtx<X>& k, const Job& jb, uint32_t
   k.cand = k.M + kRegPlane;
   k.xtop = k.cand + kRegPlane;
   k.xbot = k.xtop + (kThreads / 32) * kTW;
-  k.halo = k.xbot + (kThreads / 32) * kTW + 2 * kPubWords;   // published area, then halo
+  k.halo2 = k.xbot + (kThreads / 32) * kTW;
+  k.halo = k.halo2 + kHaloWords;
   k.pb = 0;
   k.warp = threadIdx.x >> 5;
   k.half = (threadIdx.x >> 4) & 1;
@@ -558,7 +595,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ order) {
   extern __shared__ uint4 smem4[];
   uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
-  __shared__ int flags[2], bcast;
+  __shared__ int flags[3];
   cg::cluster_group cl = cg::this_cluster();
   const int csize = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
@@ -566,13 +603,13 @@ hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ o
   const int ntx = tiles_x(jb.w);
   TileCtx<ClusterX> k;
   tile_init(k, jb, smem, rank % ntx, rank / ntx);
-  k.x.pub = k.xbot + (kThreads / 32) * kTW;
+  k.x.halo2 = k.halo2;
   k.x.Fc = k.g.F;
   k.x.flags = flags;
   k.x.slot = 0;
-  k.x.bcast = &bcast;
-  if (threadIdx.x == 0) flags[0] = flags[1] = 0;
-  cl.sync();
+  for (int t = threadIdx.x; t < kTileSmemWords; t += blockDim.x) smem[t] = 0u;
+  if (threadIdx.x == 0) flags[0] = flags[1] = flags[2] = 0;
+  cl.sync();   // every tile's halo is zero before any neighbour stores into it
   if (jb.conn == 4) tile_job<4>(k, jb, smem);
   else tile_job<8>(k, jb, smem);
   cl.sync();   // no CTA leaves while others may still read its shared memory
@@ -594,6 +631,8 @@ hasf_tile_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ cta
   k.x.gm.nctas = jb.gang;
   k.x.gm.flag_smem = &flag;
   k.x.gm.dead = 0;
+  for (int t = threadIdx.x; t < kTileSmemWords; t += blockDim.x) smem[t] = 0u;
+  __syncthreads();
   if (jb.conn == 4) tile_job<4>(k, jb, smem);
   else tile_job<8>(k, jb, smem);
 }
