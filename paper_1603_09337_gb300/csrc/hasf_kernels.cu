@@ -73,48 +73,66 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Gang barrier: sync[0] = arrivals, sync[1] = generation, sync[4..7] = OR
-// slots indexed by generation mod 4.  Every wait is bounded by a deadline;
-// a CTA that gives up marks the gang failed and leaves the job.
+// Gang barrier on two 64-bit counters at sync[4..5] and sync[6..7] (zeroed
+// before the launch), barrier e using counter e & 1.  A CTA arrives by adding
+// 1 + (its OR bit << 32) and waits until the low half reaches the arrivals
+// that barrier completes; the high half then says how many CTAs had the bit
+// set, and the OR is whether it grew since the last barrier on that counter.
+// No CTA can arrive on a counter again before every CTA has left the barrier
+// that used it, so the value a CTA reads after the wait is that barrier's
+// final value.  Every wait is bounded by a deadline; a CTA that gives up
+// marks the gang failed and leaves the job.
 struct GangMode {
   unsigned* sync_words;
   int nctas;
   int* flag_smem;  // shared int: broadcast of the barrier result
   int dead;
+  unsigned epoch;        // barriers passed (thread 0's copy is the one used)
+  unsigned hi0, hi1;     // high half after the last barrier on each counter
   static constexpr unsigned long long kDeadlineNs = 4000000000ull;
 
   static __device__ __forceinline__ uint32_t ld(const uint32_t* p) { return __ldcg(p); }
   static __device__ __forceinline__ void st(uint32_t* p, uint32_t v) { __stcg(p, v); }
   static __device__ __forceinline__ void atomic_or(uint32_t* p, uint32_t v) { atomicOr(p, v); }
 
+  __device__ __forceinline__ void init(unsigned* words, int n, int* flag) {
+    sync_words = words;
+    nctas = n;
+    flag_smem = flag;
+    dead = 0;
+    epoch = 0;
+    hi0 = hi1 = 0;
+  }
+
   __device__ int barrier(int v) {
-    int any = __syncthreads_or(v);
+    const int any = __syncthreads_or(v);
     if (threadIdx.x == 0) {
-      volatile unsigned* gen = sync_words + 1;
-      unsigned g = *gen;
-      if (any) atomicOr(sync_words + 4 + (g & 3u), 1u);
+      const unsigned par = epoch & 1u;
+      unsigned long long* ctr = reinterpret_cast<unsigned long long*>(sync_words + 4) + par;
+      const unsigned target = (epoch / 2u + 1u) * (unsigned)nctas;
       __threadfence();
-      unsigned arrived = atomicAdd(sync_words, 1u);
+      atomicAdd(ctr, 1ull | ((unsigned long long)(any != 0) << 32));
+      unsigned long long c = *(volatile unsigned long long*)ctr;
       int res = 1;
-      if (arrived == (unsigned)nctas - 1u) {
-        sync_words[0] = 0u;
-        sync_words[4 + ((g + 2u) & 3u)] = 0u;
-        __threadfence();
-        atomicExch(sync_words + 1, g + 1u);
-      } else {
-        unsigned long long t0 = global_ns();
+      if ((unsigned)c < target) {
+        const unsigned long long t0 = global_ns();
         unsigned spins = 0;
-        while (*gen == g) {
+        do {
+          __nanosleep(32);
+          c = *(volatile unsigned long long*)ctr;
+          if ((unsigned)c >= target) break;
           if ((++spins & 255u) == 0u && global_ns() - t0 > kDeadlineNs) { res = 0; break; }
-          __nanosleep(64);
-        }
+        } while (true);
       }
       __threadfence();
-      int out = res ? (int)(*(volatile unsigned*)(sync_words + 4 + (g & 3u)) != 0u) : -1;
-      *flag_smem = out;
+      const unsigned hi = (unsigned)(c >> 32);
+      *flag_smem = res ? (int)(hi != (par ? hi1 : hi0)) : -1;
+      if (par) hi1 = hi;
+      else hi0 = hi;
+      ++epoch;
     }
     __syncthreads();
-    int r = *flag_smem;
+    const int r = *flag_smem;
     __syncthreads();
     if (r < 0) dead = 1;
     return r > 0;
@@ -581,10 +599,7 @@ hasf_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) 
   const int2 m = ctamap[blockIdx.x];
   const Job& jb = jobs[m.x];
   Ctx<GangMode> k;
-  k.m.sync_words = jb.sync;
-  k.m.nctas = jb.gang;
-  k.m.flag_smem = &flag;
-  k.m.dead = 0;
+  k.m.init(jb.sync, jb.gang, &flag);
   init_ctx(k, jb, jb.planes, m.y * blockDim.x + threadIdx.x, jb.gang * blockDim.x);
   if (jb.conn == 4) run_job<GangMode, 4>(k, jb, jb.planes);
   else run_job<GangMode, 8>(k, jb, jb.planes);
