@@ -127,9 +127,10 @@ class ClockSampler:
 
 def _oracle_job(args):
     import oracle
-    X, C, rmax = args
+    X, C, rmax = args[:3]
+    conn = args[3] if len(args) > 3 else 8
     t = time.perf_counter()
-    oracle.hasf(X, rmax, C=C)
+    oracle.hasf(X, rmax, C=C, conn=conn)
     return time.perf_counter() - t
 
 
@@ -145,7 +146,7 @@ def cpu_oracle_rate(jobs, cores):
     with _pool(cores) as pool:
         pool.map(_oracle_job, [(jobs[0].X, jobs[0].C, jobs[0].rmax)] * cores)  # warm workers
         t0 = time.perf_counter()
-        per = pool.map(_oracle_job, [(j.X, j.C, j.rmax) for j in jobs], chunksize=1)
+        per = pool.map(_oracle_job, [(j.X, j.C, j.rmax, j.conn) for j in jobs], chunksize=1)
         wall = time.perf_counter() - t0
     return len(jobs) / wall, wall, sum(per)
 
@@ -330,11 +331,17 @@ def run_hasf(args):
         jobs = [synth.large_image(args.side)]
         workload = f"one {args.side}x{args.side} image of 2,000 discs/ellipses, 3% noise, rmax=10"
         metric = f"HASF images/s at {args.side}x{args.side}, rmax=10"
+    if args.conn == 4:
+        for j in jobs:
+            j.conn = 4
+        workload += "; (4,8) adjacency"
+        metric += ", (4,8)"
     n = len(jobs)
     Xs = [torch.from_numpy(j.X).to(dev) for j in jobs]
     Cs = [torch.from_numpy(j.C).to(dev) if j.C is not None else None for j in jobs]
     outs = [torch.empty_like(x) for x in Xs]
-    imgs = [Image(Xs[i], jobs[i].rmax, C=Cs[i], out=outs[i]) for i in range(n)]
+    imgs = [Image(Xs[i], jobs[i].rmax, C=Cs[i], out=outs[i], conn=jobs[i].conn)
+            for i in range(n)]
     arr = ctx.batch_descriptors(imgs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -379,6 +386,28 @@ def run_hasf(args):
     value = n * args.steps * ws / (t_ms / 1e3)
     ms_per_step = t_ms / args.steps
 
+    # The same step as plain per-image launches: one hasf_smooth per image on
+    # the same stream (the alternative to the batched launch).
+    per_image = None
+    if args.workload != "large":
+        for i in range(n):
+            ctx.smooth(Xs[i], jobs[i].rmax, C=Cs[i], out=outs[i], conn=jobs[i].conn)
+        ctx.status()
+        k = 1 if args.workload == "ragged" else max(1, min(args.steps, 3))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        barrier()
+        a.record(stream)
+        for _ in range(k):
+            for i in range(n):
+                ctx.smooth(Xs[i], jobs[i].rmax, C=Cs[i], out=outs[i], conn=jobs[i].conn)
+        b.record(stream)
+        barrier()
+        ctx.status()
+        tp = replicas.max_over_ranks(a.elapsed_time(b) / k, dev)
+        per_image = {"value": n * ws / (tp / 1e3), "unit": "images/s", "ms_per_step": tp,
+                     "launches_per_step": n, "steps": k}
+
     # End to end through the host-buffer entry point with pinned host buffers:
     # H2D of X and C, the smoothing, D2H of the result, every step.
     e2e = None
@@ -387,7 +416,7 @@ def run_hasf(args):
         hC = [torch.from_numpy(j.C).pin_memory().numpy() if j.C is not None else None
               for j in jobs]
         hO = [torch.empty(j.X.shape, dtype=torch.uint8).pin_memory().numpy() for j in jobs]
-        host_jobs = [(hX[i], jobs[i].rmax, hC[i], None, 8, hO[i]) for i in range(n)]
+        host_jobs = [(hX[i], jobs[i].rmax, hC[i], None, jobs[i].conn, hO[i]) for i in range(n)]
         ctx.smooth_host(host_jobs)                     # warm-up
         k = max(1, min(args.steps, 5))
         barrier()
@@ -426,13 +455,29 @@ def run_hasf(args):
            "peak_source": peak_src, "algorithmic_bytes_per_step": alg_bytes}
 
     cpu = None
-    if not args.no_cpu and ws == 1 and args.workload == "batch512":
+    if not args.no_cpu and ws == 1 and args.workload != "large":
         cores = os.cpu_count() or 1
-        sample = synth.batch_512(2 * cores, first=10_000)
+        if args.workload == "batch512":
+            sample = synth.batch_512(2 * cores, first=10_000)
+        else:
+            sample = synth.ragged_batch(cores, first=100_000)
+        for j in sample:
+            j.conn = args.conn
         rate, cwall, cwork = cpu_oracle_rate(sample, cores)
         cpu = {"value": rate, "unit": "images/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(sample)} images of the workload (other seeds), one oracle "
                          f"process per core, {cwork:.1f} s of CPU work in {cwall:.1f} s"}
+    elif not args.no_cpu and ws == 1:
+        # One full image takes the oracle minutes: time a 1024 x 1024 window of
+        # it instead and scale by pixels (the work per pixel of a window is
+        # that of the whole image up to border effects).
+        cores = os.cpu_count() or 1
+        win = jobs[0].X[:1024, :1024].copy()
+        rate_w, cwall, cwork = cpu_oracle_rate([synth.Job(win, jobs[0].rmax, conn=args.conn)], 1)
+        scale = win.size / jobs[0].X.size
+        cpu = {"value": rate_w * scale, "unit": "images/s", "cores": 1, "kind": "oracle",
+               "sample": f"one 1024x1024 window of the image, rmax {jobs[0].rmax}, one core, "
+                         f"{cwork:.1f} s; images/s scaled by the pixel ratio {scale:.4f}"}
 
     px = sum(x.numel() for x in Xs)
     line = {
@@ -445,7 +490,8 @@ def run_hasf(args):
                    "l2": "flushed between timed steps (256 MB write, untimed)",
                    "launch": "CUDA graph replay" if args.graph else "hasf_smooth_batch",
                    "mpixel_per_s": px * args.steps * ws / (t_ms / 1e3) / 1e6, "wall_s": wall},
-        "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
+        "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
+        "per_image_launches": per_image, "serving": serving,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -469,6 +515,8 @@ def main():
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--conn", type=int, default=8, choices=[8, 4],
+                    help="adjacency of the object: 8 = (8,4), 4 = (4,8)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

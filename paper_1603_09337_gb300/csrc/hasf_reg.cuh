@@ -78,9 +78,9 @@ struct RegCtx {
 // marked.  A change in row r marks rows r - 1 and r + 1 (the strips of a warp
 // are stacked, so row 15 and row 0 are neighbours across them).  Returns the
 // OR of the changed bits.
-template <int CONN, int SY>
-__device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], bool thin,
-                                             uint32_t above, uint32_t below, uint32_t& need) {
+template <int CONN, int SY, bool thin>
+__device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], uint32_t above,
+                                             uint32_t below, uint32_t& need) {
   const int j = k.j;
   uint32_t* cr = k.cand + k.s0 * kRegPitch + j;
   uint32_t changed = 0;
@@ -106,11 +106,11 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], bo
     const uint32_t chg0 = cw & 0x55555555u & sm;
     const bool any0 = __any_sync(0xFFFFFFFFu, chg0 != 0u);
     if (any0) {
+      // odd pixels see only their own word's even pixels on the left, so
+      // only the right neighbour's (updated) word is fetched again
       c = thin ? (c & ~chg0) : (c | chg0);
       cw &= ~chg0;
-      wv = __shfl_up_sync(0xFFFFFFFFu, c, 1, 16);
       e = __shfl_down_sync(0xFFFFFFFFu, c, 1, 16);
-      if (j == 0) wv = 0u;
       if (j == kRegW - 1) e = 0u;
       sm = simple_bits<CONN>(nw, n, ne, wv, c, e, sw, s, se);
     }
@@ -141,9 +141,9 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], bo
 
 // Rounds at one level until a round changes nothing.  False on the cap.
 // ab_prev / be_prev: the rows across the warp boundary as last seen.
-template <int CONN>
-__device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], bool thin, uint32_t& need,
-                          uint32_t& ab_prev, uint32_t& be_prev) {
+template <int CONN, bool thin>
+__device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint32_t& ab_prev,
+                          uint32_t& be_prev) {
   const int lane = threadIdx.x & 31;
   for (int round = 0;; ++round) {
     if (round >= k.g.cap) return false;
@@ -155,7 +155,7 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], bool thin, uint32_t& 
     if (__any_sync(0xFFFFFFFFu, ab != ab_prev)) need |= 1u;
     ab_prev = ab;
     k.g.n_tests += 2 * __popc(need & 0x5555u);
-    uint32_t ch = reg_half<CONN, 0>(k, S, thin, ab, 0u, need);
+    uint32_t ch = reg_half<CONN, 0, thin>(k, S, ab, 0u, need);
     if (k.half == 0) k.top[k.warp * kRegW + k.j] = S[0];
     __syncthreads();
     // odd rows: row below the strip = first row of the strip below
@@ -165,7 +165,7 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], bool thin, uint32_t& 
     if (__any_sync(0xFFFFFFFFu, be != be_prev)) need |= 0x8000u;
     be_prev = be;
     k.g.n_tests += 2 * __popc(need & 0xAAAAu);
-    ch |= reg_half<CONN, 1>(k, S, thin, 0u, be, need);
+    ch |= reg_half<CONN, 1, thin>(k, S, 0u, be, need);
     if (k.half == 1) k.bot[k.warp * kRegW + k.j] = S[kRegR - 1];
     if (!__syncthreads_or(ch != 0u)) return true;
   }
@@ -180,8 +180,8 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], bool thin, uint32_t& 
 
 // One constrained thinning (thin) or thickening at radius r; the allowed
 // points are (thin ? S : complement of S) cap pos minus neg (global planes).
-template <int CONN>
-__device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r, bool thin,
+template <int CONN, bool thin>
+__device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r,
                              const uint32_t* pos, const uint32_t* neg) {
   Ctx<SmemMode>& g = k.g;
   // snapshot F, the movable mask M, no candidates; rows with movable points
@@ -271,7 +271,7 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r, bool thin,
     need |= __reduce_or_sync(0xFFFFFFFFu, newrows);
     if (!__syncthreads_or(newrows != 0u)) continue;
     ++g.n_levels;
-    if (!reg_level<CONN>(k, S, thin, need, ab_prev, be_prev)) return false;
+    if (!reg_level<CONN, thin>(k, S, need, ab_prev, be_prev)) return false;
   }
   return true;
 }
@@ -339,13 +339,13 @@ __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
   bool ok = true;
   auto hc = [&](int r) {
     snapshot_g0();
-    if (!reg_operator<CONN>(k, S, r, true, nullptr, jb.cp)) return false;
-    return reg_operator<CONN>(k, S, r, false, jb.g0, nullptr);
+    if (!reg_operator<CONN, true>(k, S, r, nullptr, jb.cp)) return false;
+    return reg_operator<CONN, false>(k, S, r, jb.g0, nullptr);
   };
   auto hf = [&](int r) {
     snapshot_g0();
-    if (!reg_operator<CONN>(k, S, r, false, nullptr, jb.dp)) return false;
-    return reg_operator<CONN>(k, S, r, true, nullptr, jb.g0);
+    if (!reg_operator<CONN, false>(k, S, r, nullptr, jb.dp)) return false;
+    return reg_operator<CONN, true>(k, S, r, nullptr, jb.g0);
   };
   switch (jb.op) {
     case OP_HASF:
@@ -354,8 +354,8 @@ __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
         if (ok) ok = hf(r);
       }
       break;
-    case OP_THIN: ok = reg_operator<CONN>(k, S, jb.r_hi, true, nullptr, jb.cp); break;
-    case OP_THICK: ok = reg_operator<CONN>(k, S, jb.r_hi, false, jb.cp, nullptr); break;
+    case OP_THIN: ok = reg_operator<CONN, true>(k, S, jb.r_hi, nullptr, jb.cp); break;
+    case OP_THICK: ok = reg_operator<CONN, false>(k, S, jb.r_hi, jb.cp, nullptr); break;
     case OP_HC: ok = hc(jb.r_hi); break;
     case OP_HF: ok = hf(jb.r_hi); break;
     default: ok = false;

@@ -234,8 +234,8 @@ __device__ int tile_exchange(TileCtx<ClusterX>& k, const uint32_t (&S)[kRegR], i
 // fused row by row as in the single-tile kernel, with the tile's left/right
 // neighbour words from the halo and the right neighbour's even pixel 0
 // recomputed for the odd pass.
-template <int CONN, int SY, class X>
-__device__ __forceinline__ uint32_t tile_half(TileCtx<X>& k, uint32_t (&S)[kRegR], bool thin,
+template <int CONN, int SY, bool thin, class X>
+__device__ __forceinline__ uint32_t tile_half(TileCtx<X>& k, uint32_t (&S)[kRegR],
                                               uint32_t above, uint32_t below) {
   const int j = k.j;
   const uint32_t* lcol = k.halo + kHLcol;   // index = tile row + 1
@@ -279,11 +279,10 @@ __device__ __forceinline__ uint32_t tile_half(TileCtx<X>& k, uint32_t (&S)[kRegR
       e1 = thin ? (e & ~cr0) : (e | cr0);
     }
     if (__any_sync(0xFFFFFFFFu, chg0 != 0u || e1 != e)) {
+      // odd pixels see only their own word's even pixels on the left
       c = thin ? (c & ~chg0) : (c | chg0);
       cw &= ~chg0;
-      wv = __shfl_up_sync(0xFFFFFFFFu, c, 1, 16);
       uint32_t e2 = __shfl_down_sync(0xFFFFFFFFu, c, 1, 16);
-      if (j == 0) wv = lcol[R + 1];
       if (j == kTW - 1) e2 = e1;
       sm = simple_bits<CONN>(nw, n, ne, wv, c, e2, sw, s, se);
     }
@@ -320,18 +319,18 @@ __device__ __forceinline__ uint32_t tile_below(TileCtx<X>& k, const uint32_t (&S
   return v;
 }
 
-template <int CONN, class X>
-__device__ bool tile_level(TileCtx<X>& k, uint32_t (&S)[kRegR], bool thin) {
+template <int CONN, bool thin, class X>
+__device__ bool tile_level(TileCtx<X>& k, uint32_t (&S)[kRegR]) {
   for (int round = 0;; ++round) {
     if (round >= k.g.cap) return false;
     ++k.g.n_rounds;
     k.g.n_passes += 4;
     k.g.n_tests += 2 * kRegR;
-    uint32_t ch = tile_half<CONN, 0>(k, S, thin, tile_above(k, S), 0u);
+    uint32_t ch = tile_half<CONN, 0, thin>(k, S, tile_above(k, S), 0u);
     if (k.half == 0) k.xtop[k.warp * kTW + k.j] = S[0];
     tile_exchange(k, S, 0);
     if (k.x.failed()) return false;
-    ch |= tile_half<CONN, 1>(k, S, thin, 0u, tile_below(k, S));
+    ch |= tile_half<CONN, 1, thin>(k, S, 0u, tile_below(k, S));
     if (k.half == 1) k.xbot[k.warp * kTW + k.j] = S[kRegR - 1];
     const int any = tile_exchange(k, S, ch != 0u);
     if (k.x.failed()) return false;
@@ -339,8 +338,8 @@ __device__ bool tile_level(TileCtx<X>& k, uint32_t (&S)[kRegR], bool thin) {
   }
 }
 
-template <int CONN, class X>
-__device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r, bool thin,
+template <int CONN, bool thin, class X>
+__device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r,
                               const uint32_t* pos, const uint32_t* neg) {
   Ctx<SmemMode>& g = k.g;
   uint32_t pendrows = 0;
@@ -444,7 +443,7 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r, bool t
     if (k.x.failed()) return false;
     if (!any) continue;
     ++g.n_levels;
-    if (!tile_level<CONN>(k, S, thin)) return false;
+    if (!tile_level<CONN, thin>(k, S)) return false;
   }
   return true;
 }
@@ -489,13 +488,13 @@ __device__ __forceinline__ void tile_job(TileCtx<X>& k, const Job& jb, uint32_t*
   bool ok = true;
   auto hc = [&](int r) {
     snapshot_g0();
-    if (!tile_operator<CONN>(k, S, r, true, nullptr, jb.cp)) return false;
-    return tile_operator<CONN>(k, S, r, false, jb.g0, nullptr);
+    if (!tile_operator<CONN, true>(k, S, r, nullptr, jb.cp)) return false;
+    return tile_operator<CONN, false>(k, S, r, jb.g0, nullptr);
   };
   auto hf = [&](int r) {
     snapshot_g0();
-    if (!tile_operator<CONN>(k, S, r, false, nullptr, jb.dp)) return false;
-    return tile_operator<CONN>(k, S, r, true, nullptr, jb.g0);
+    if (!tile_operator<CONN, false>(k, S, r, nullptr, jb.dp)) return false;
+    return tile_operator<CONN, true>(k, S, r, nullptr, jb.g0);
   };
   switch (jb.op) {
     case OP_HASF:
@@ -504,8 +503,8 @@ __device__ __forceinline__ void tile_job(TileCtx<X>& k, const Job& jb, uint32_t*
         if (ok) ok = hf(r);
       }
       break;
-    case OP_THIN: ok = tile_operator<CONN>(k, S, jb.r_hi, true, nullptr, jb.cp); break;
-    case OP_THICK: ok = tile_operator<CONN>(k, S, jb.r_hi, false, jb.cp, nullptr); break;
+    case OP_THIN: ok = tile_operator<CONN, true>(k, S, jb.r_hi, nullptr, jb.cp); break;
+    case OP_THICK: ok = tile_operator<CONN, false>(k, S, jb.r_hi, jb.cp, nullptr); break;
     case OP_HC: ok = hc(jb.r_hi); break;
     case OP_HF: ok = hf(jb.r_hi); break;
     default: ok = false;
