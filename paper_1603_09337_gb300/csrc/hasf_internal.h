@@ -81,6 +81,8 @@ inline size_t resident_smem_bytes(int w, int h) { return state_bytes(w, h); }
 
 // Host launchers (hasf_kernels.cu).
 cudaError_t upload_level_table();
+cudaError_t set_level_table_reg(const void* tab, size_t bytes);
+cudaError_t set_level_table_tiled(const void* tab, size_t bytes);
 cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, int grid,
                             size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
 cudaError_t launch_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);

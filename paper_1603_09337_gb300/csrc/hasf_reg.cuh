@@ -1,5 +1,5 @@
 // hasf_reg.cuh -- register-resident fused HASF kernel for images up to
-// 512 x 512 (included by hasf_kernels.cu, which defines the helpers it uses).
+// 512 x 512 (device code; included by hasf_reg.cu and hasf_tiled.cu after hasf_device.cuh).
 //
 // The current set S lives in registers (the candidates, read once per test,
 // in shared memory).  With 16 words (512 pixels) per row,
@@ -296,6 +296,48 @@ __device__ __forceinline__ uint32_t pack_word(const uint8_t* p, int n, bool vec)
   return v;
 }
 
+// A job as a sequence of constrained operators.  HC_r (eq. (i)) is a
+// thinning that keeps C, then a thickening inside its input g0; HF_r (eq.
+// (ii)) a thickening that avoids D, then a thinning that keeps g0.  pos: the
+// points that may change must lie in it; neg: they must not.  snap: g0 is
+// taken (the current set) before the step.
+struct OpStep {
+  int r;
+  bool thin, snap;
+  const uint32_t* pos;
+  const uint32_t* neg;
+};
+__device__ __forceinline__ int op_steps(const Job& jb) {
+  switch (jb.op) {
+    case OP_HASF: return 4 * (jb.r_hi - jb.r_lo + 1);
+    case OP_HC:
+    case OP_HF: return 2;
+    case OP_THIN:
+    case OP_THICK: return 1;
+    default: return 0;
+  }
+}
+__device__ __forceinline__ OpStep op_step(const Job& jb, int st) {
+  int kind, r = jb.r_hi;  // kind 0/1: HC thin/thick, 2/3: HF thick/thin, 4: thin, 5: thick
+  if (jb.op == OP_HASF) {
+    kind = st & 3;
+    r = jb.r_lo + (st >> 2);
+  } else if (jb.op == OP_HC) {
+    kind = st;
+  } else if (jb.op == OP_HF) {
+    kind = 2 + st;
+  } else {
+    kind = jb.op == OP_THIN ? 4 : 5;
+  }
+  OpStep s;
+  s.r = r;
+  s.thin = kind == 0 || kind == 3 || kind == 4;
+  s.snap = kind == 0 || kind == 2;
+  s.pos = kind == 1 ? jb.g0 : (kind == 5 ? jb.cp : nullptr);
+  s.neg = (kind == 0 || kind == 4) ? jb.cp : (kind == 2 ? jb.dp : (kind == 3 ? jb.g0 : nullptr));
+  return s;
+}
+
 template <int CONN>
 __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
   Ctx<SmemMode>& g = k.g;
@@ -402,48 +444,6 @@ __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
       atomicAdd(jb.stats + STAT_LEVELS, (unsigned long long)g.n_levels);
       atomicAdd(jb.stats + STAT_ROUNDS, (unsigned long long)g.n_rounds);
     }
-  }
-}
-
-// Persistent CTAs of kThreads threads take register-path jobs from `order`.
-__global__ void __launch_bounds__(kThreads, 2)
-hasf_reg_kernel(const Job* __restrict__ jobs, const int* __restrict__ order, int njobs,
-                unsigned* counter) {
-  extern __shared__ uint4 smem4[];
-  uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
-  __shared__ int next;
-  for (;;) {
-    if (threadIdx.x == 0) next = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    const int slot = next;
-    __syncthreads();
-    if (slot >= njobs) break;
-    const Job& jb = jobs[order[slot]];
-    RegCtx k;
-    Ctx<SmemMode>& g = k.g;
-    g.w = jb.w;
-    g.h = jb.h;
-    g.wpr = jb.wpr;
-    g.P = row_pitch(jb.w);
-    const int rem = jb.w & 31;
-    g.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
-    g.S = nullptr;
-    g.F = smem + 1 + kRegPadR * g.P;
-    g.cand = nullptr;
-    g.cap = jb.cap;
-    g.n_tests = g.n_ring = g.n_passes = g.n_levels = g.n_rounds = 0;
-    k.M = smem + reg_f_words(jb.w, jb.h);
-    k.cand = k.M + kRegPlane;
-    k.top = k.cand + kRegPlane;
-    k.bot = k.top + (kThreads / 32) * kRegW;
-    k.warp = threadIdx.x >> 5;
-    k.half = (threadIdx.x >> 4) & 1;
-    k.j = threadIdx.x & 15;
-    k.s0 = (2 * k.warp + k.half) * kRegR;
-    k.jin = k.j < jb.wpr;
-    if (jb.conn == 4) reg_job<4>(k, jb, smem);
-    else reg_job<8>(k, jb, smem);
-    __syncthreads();
   }
 }
 

@@ -1,5 +1,5 @@
 // hasf_tiled.cuh -- register-resident HASF for images larger than one tile
-// (included by hasf_kernels.cu after hasf_reg.cuh, whose helpers it uses).
+// (device code; included by hasf_tiled.cu after hasf_reg.cuh, whose helpers it uses).
 //
 // The image is cut into tiles of 512 x 512 pixels (16 words x 512 rows), one
 // CTA per tile, each running the register scheme of the single-tile kernel:
@@ -485,29 +485,14 @@ __device__ __forceinline__ void tile_job(TileCtx<X>& k, const Job& jb, uint32_t*
     }
     __syncthreads();
   };
-  bool ok = true;
-  auto hc = [&](int r) {
-    snapshot_g0();
-    if (!tile_operator<CONN, true>(k, S, r, nullptr, jb.cp)) return false;
-    return tile_operator<CONN, false>(k, S, r, jb.g0, nullptr);
-  };
-  auto hf = [&](int r) {
-    snapshot_g0();
-    if (!tile_operator<CONN, false>(k, S, r, nullptr, jb.dp)) return false;
-    return tile_operator<CONN, true>(k, S, r, nullptr, jb.g0);
-  };
-  switch (jb.op) {
-    case OP_HASF:
-      for (int r = jb.r_lo; ok && r <= jb.r_hi; ++r) {
-        ok = hc(r);
-        if (ok) ok = hf(r);
-      }
-      break;
-    case OP_THIN: ok = tile_operator<CONN, true>(k, S, jb.r_hi, nullptr, jb.cp); break;
-    case OP_THICK: ok = tile_operator<CONN, false>(k, S, jb.r_hi, jb.cp, nullptr); break;
-    case OP_HC: ok = hc(jb.r_hi); break;
-    case OP_HF: ok = hf(jb.r_hi); break;
-    default: ok = false;
+  // one call site per operator kind keeps the kernel small
+  const int nst = op_steps(jb);
+  bool ok = nst > 0;
+  for (int st = 0; ok && st < nst; ++st) {
+    const OpStep o = op_step(jb, st);
+    if (o.snap) snapshot_g0();
+    ok = o.thin ? tile_operator<CONN, true>(k, S, o.r, o.pos, o.neg)
+                : tile_operator<CONN, false>(k, S, o.r, o.pos, o.neg);
   }
   if (ok) {
     const bool vec = ((reinterpret_cast<uintptr_t>(jb.out) | (uintptr_t)jb.pitch) & 15u) == 0;
@@ -587,50 +572,6 @@ __device__ __forceinline__ void tile_init(TileCtx<X>& k, const Job& jb, uint32_t
   k.x.nty = tiles_y(jb.h);
   k.x.tx = tx;
   k.x.ty = ty;
-}
-
-// One cluster of ntx * nty CTAs per image: cluster i works on job order[i].
-__global__ void __launch_bounds__(kThreads, 1)
-hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ order) {
-  extern __shared__ uint4 smem4[];
-  uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
-  __shared__ int flags[3];
-  cg::cluster_group cl = cg::this_cluster();
-  const int csize = (int)cl.num_blocks();
-  const int rank = (int)cl.block_rank();
-  const Job& jb = jobs[order[blockIdx.x / csize]];
-  const int ntx = tiles_x(jb.w);
-  TileCtx<ClusterX> k;
-  tile_init(k, jb, smem, rank % ntx, rank / ntx);
-  k.x.halo2 = k.halo2;
-  k.x.Fc = k.g.F;
-  k.x.flags = flags;
-  k.x.slot = 0;
-  for (int t = threadIdx.x; t < kTileSmemWords; t += blockDim.x) smem[t] = 0u;
-  if (threadIdx.x == 0) flags[0] = flags[1] = flags[2] = 0;
-  cl.sync();   // every tile's halo is zero before any neighbour stores into it
-  if (jb.conn == 4) tile_job<4>(k, jb, smem);
-  else tile_job<8>(k, jb, smem);
-  cl.sync();   // no CTA leaves while others may still read its shared memory
-}
-
-// Gang mode with tiles: CTA b works on tile ctamap[b].y of job ctamap[b].x.
-__global__ void __launch_bounds__(kThreads, 1)
-hasf_tile_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) {
-  extern __shared__ uint4 smem4[];
-  uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
-  __shared__ int flag;
-  const int2 m = ctamap[blockIdx.x];
-  const Job& jb = jobs[m.x];
-  const int ntx = tiles_x(jb.w);
-  TileCtx<GangX> k;
-  tile_init(k, jb, smem, m.y % ntx, m.y / ntx);
-  k.x.gbase = jb.planes;
-  k.x.gm.init(jb.sync, jb.gang, &flag);
-  for (int t = threadIdx.x; t < kTileSmemWords; t += blockDim.x) smem[t] = 0u;
-  __syncthreads();
-  if (jb.conn == 4) tile_job<4>(k, jb, smem);
-  else tile_job<8>(k, jb, smem);
 }
 
 }  // namespace hasf
