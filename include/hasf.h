@@ -61,15 +61,26 @@ typedef enum {
     HASF_ETIMEOUT = 5,    /* a device iteration cap or wait deadline hit    */
     HASF_ECUDA = 6,       /* a CUDA runtime call failed                     */
     HASF_ENOTFOUND = 7,   /* unknown ticket                                 */
-    HASF_ECANCELLED = 8   /* the job was cancelled before it ran            */
+    HASF_ECANCELLED = 8,  /* the job was cancelled before it ran            */
+    HASF_EUNSTABLE = 9    /* run to stability: still changing at the cap    */
 } hasf_status;
+
+/* rmax for the filter run to stability with the largest cap (see hasf_image). */
+#define HASF_RMAX_STABLE (-64)
 
 /* One image to smooth.  in/out/C/D share `pitch`.  out may equal in.
  * C == NULL means C is empty; C is used as C cap X (Sec. 2 requires C within X).
  * D == NULL means D is empty; D is used as D minus X (Sec. 2 requires D in the
  * complement of X).  width, height in [1, 65536]; pitch >= width;
  * rmax in [1, 64] is the order n of the filter; connectivity is 8 for
- * (8,4) adjacency (8-connected object, 4-connected background) or 4 for (4,8). */
+ * (8,4) adjacency (8-connected object, 4-connected background) or 4 for (4,8).
+ * rmax in [-64, -1] runs the filter to stability, the reading taken of the
+ * unbounded radius ("r = infinity") of Table 1: steps r = 1, 2, ... (each
+ * HC_r^C then HF_r^D) until one leaves the image unchanged, at most -rmax
+ * steps.  out receives the image after the last step run; if step -rmax still
+ * changed it, the job's status is HASF_EUNSTABLE (reported like
+ * HASF_ETIMEOUT; a timeout takes precedence).  Such images run on the generic
+ * kernels, with one more h * ceil(w / 32)-word plane of scratch. */
 typedef struct hasf_image {
     const uint8_t *in;
     uint8_t *out;
@@ -108,7 +119,8 @@ int hasf_smooth(hasf_ctx *ctx, const hasf_image *img, void *stream);
 int hasf_smooth_batch(hasf_ctx *ctx, const hasf_image *imgs, int n, void *stream);
 
 /* Synchronise `stream` and report the device status of the context's last
- * launches on it: HASF_OK or HASF_ETIMEOUT (and clear it), or HASF_ECUDA. */
+ * launches on it: HASF_OK, HASF_ETIMEOUT or HASF_EUNSTABLE (and clear it), or
+ * HASF_ECUDA. */
 int hasf_status_of(hasf_ctx *ctx, void *stream);
 
 /* Host-buffer form: every pointer in `imgs` is a HOST pointer (ordinary or

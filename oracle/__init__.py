@@ -72,9 +72,11 @@ def load():
             lib.hasf_oracle_hc.argtypes = [u8p, u8p, ci, ci, ci, ci, sp]
             lib.hasf_oracle_hf.argtypes = [u8p, u8p, ci, ci, ci, ci, sp]
             lib.hasf_oracle_hasf.argtypes = [u8p, u8p, u8p, ci, ci, ci, ci, u8p, sp]
+            lib.hasf_oracle_hasf_stable.argtypes = [u8p, u8p, u8p, ci, ci, ci, ci, u8p, sp]
             for name in ("hasf_oracle_simple_lut", "hasf_oracle_edt", "hasf_oracle_dilate",
                          "hasf_oracle_erode", "hasf_oracle_thin", "hasf_oracle_thicken",
-                         "hasf_oracle_hc", "hasf_oracle_hf", "hasf_oracle_hasf"):
+                         "hasf_oracle_hc", "hasf_oracle_hf", "hasf_oracle_hasf",
+                         "hasf_oracle_hasf_stable"):
                 getattr(lib, name).restype = ci
             lib.hasf_oracle_stats_size.restype = ci
             assert lib.hasf_oracle_stats_size() == ctypes.sizeof(Stats)
@@ -192,3 +194,24 @@ def hasf(X, rmax: int, C=None, D=None, conn: int = 8, stats: Stats | None = None
                                    w, h, rmax, conn, _p(out, ctypes.c_uint8),
                                    ctypes.byref(stats) if stats is not None else None), "hasf")
     return out
+
+
+def hasf_stable(X, rcap: int = 64, C=None, D=None, conn: int = 8,
+                stats: Stats | None = None) -> tuple[np.ndarray, int]:
+    """HASF steps r = 1, 2, ... until one leaves the image unchanged (at most
+    rcap steps).  Returns (image, r) with r the radius of the step that changed
+    nothing, or 0 if step rcap still changed the image."""
+    x = _u8(X)
+    h, w = x.shape
+    c = _u8(C) if C is not None else None
+    d = _u8(D) if D is not None else None
+    out = np.zeros_like(x)
+    r = load().hasf_oracle_hasf_stable(_p(x, ctypes.c_uint8),
+                                      _p(c, ctypes.c_uint8) if c is not None else None,
+                                      _p(d, ctypes.c_uint8) if d is not None else None,
+                                      w, h, rcap, conn, _p(out, ctypes.c_uint8),
+                                      ctypes.byref(stats) if stats is not None else None)
+    if r < 0:
+        raise ValueError("hasf_stable: bad arguments")
+    return out, r
+

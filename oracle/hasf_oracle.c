@@ -483,5 +483,51 @@ int hasf_oracle_hasf(const uint8_t *in, const uint8_t *C, const uint8_t *D, int 
     return rc;
 }
 
+/* HASF run to stability: the order of the filter is not given; steps
+ * r = 1, 2, ... (each HC_r^C then HF_r^D, as in hasf_oracle_hasf) are applied
+ * until one leaves the image unchanged, at most rcap steps.  This is the
+ * reading taken of the unbounded radius ("r = infinity") of Table 1.
+ * out receives the image after the last step applied.  Returns the radius of
+ * the step that changed nothing (the image is a fixed point of that step),
+ * 0 if step rcap still changed the image, or -1 on bad arguments. */
+int hasf_oracle_hasf_stable(const uint8_t *in, const uint8_t *C, const uint8_t *D, int w,
+                            int h, int rcap, int conn, uint8_t *out, hasf_oracle_stats *st)
+{
+    if (w < 1 || h < 1 || rcap < 1 || (conn != 8 && conn != 4)) return -1;
+    size_t n = (size_t)w * h;
+    uint8_t *X = (uint8_t *)malloc(n), *prev = (uint8_t *)malloc(n), *Cx = NULL, *Dx = NULL;
+    if (!X || !prev) { free(X); free(prev); return -1; }
+    for (size_t p = 0; p < n; ++p) X[p] = in[p] ? 1 : 0;
+    if (C) {
+        Cx = (uint8_t *)malloc(n);
+        if (!Cx) { free(X); free(prev); return -1; }
+        for (size_t p = 0; p < n; ++p) Cx[p] = C[p] && X[p];
+    }
+    if (D) {
+        Dx = (uint8_t *)malloc(n);
+        if (!Dx) { free(X); free(prev); free(Cx); return -1; }
+        for (size_t p = 0; p < n; ++p) Dx[p] = D[p] && !X[p];
+    }
+    int result = 0;
+    for (int r = 1; r <= rcap; ++r) {
+        memcpy(prev, X, n);
+        if (hasf_oracle_hc(X, Cx, w, h, r, conn, st) != 0 ||
+            hasf_oracle_hf(X, Dx, w, h, r, conn, st) != 0) {
+            result = -1;
+            break;
+        }
+        if (memcmp(prev, X, n) == 0) {
+            result = r;
+            break;
+        }
+    }
+    if (result >= 0) memcpy(out, X, n);
+    free(X);
+    free(prev);
+    free(Cx);
+    free(Dx);
+    return result;
+}
+
 /* Size of the statistics record, so that callers can check their layout. */
 int hasf_oracle_stats_size(void) { return (int)sizeof(hasf_oracle_stats); }

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhasf.so")
 
 HASF_OK, HASF_EINVAL, HASF_ENOMEM, HASF_EBUDGET, HASF_EPENDING = 0, 1, 2, 3, 4
 HASF_ETIMEOUT, HASF_ECUDA, HASF_ENOTFOUND, HASF_ECANCELLED = 5, 6, 7, 8
+HASF_EUNSTABLE = 9
+RMAX_STABLE = -64   # rmax < 0: run to stability, at most -rmax steps
 
 OPT_FORCE_GANG, OPT_GANG_CTAS, OPT_ROUND_CAP, OPT_SERVE_STREAMS, OPT_SERVE_BATCH = 1, 2, 3, 4, 5
 OPT_STATS = 6

@@ -34,12 +34,22 @@ namespace {
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
+// Public status of a device status word.
+int public_status(int dev) {
+  switch (dev) {
+    case DEV_OK: return HASF_OK;
+    case DEV_UNSTABLE: return HASF_EUNSTABLE;
+    case DEV_TIMEOUT: return HASF_ETIMEOUT;
+    default: return HASF_ECUDA;
+  }
+}
+
 int validate(const hasf_image* im) {
   if (!im || !im->in || !im->out) return HASF_EINVAL;
   if (im->width < 1 || im->width > 65536 || im->height < 1 || im->height > 65536)
     return HASF_EINVAL;
   if (im->pitch < im->width) return HASF_EINVAL;
-  if (im->rmax < 1 || im->rmax > kMaxR) return HASF_EINVAL;
+  if (im->rmax == 0 || im->rmax > kMaxR || im->rmax < -kMaxR) return HASF_EINVAL;
   if (im->connectivity != 8 && im->connectivity != 4) return HASF_EINVAL;
   if (im->reserved != 0) return HASF_EINVAL;
   return HASF_OK;
@@ -169,6 +179,7 @@ bool fits_resident(const hasf_ctx* ctx, const hasf_image& im) {
 // cluster, 2 = tiled gang, 0 = the generic kernels.
 int tile_path(const hasf_ctx* ctx, const hasf_image& im) {
   if (ctx->opt.force_gang || ctx->opt.generic_only || ctx->opt.no_tiles) return 0;
+  if (im.rmax < 0) return 0;  // run to stability: the generic kernels
   if (im.rmax > kTileMaxR) return 0;
   auto it = ctx->tune.find(tune_key(im));
   if (it != ctx->tune.end() && it->second >= 0) return 0;  // tuned to a generic shape
@@ -186,7 +197,8 @@ bool wants_gang(const hasf_ctx* ctx, const hasf_image& im) {
   return it != ctx->tune.end() && it->second > 0 && !reg_kernel_ok(im.width, im.height, im.rmax);
 }
 bool uses_reg(const hasf_ctx* ctx, const hasf_image& im) {
-  return !ctx->opt.force_gang && !ctx->opt.generic_only && reg_kernel_ok(im.width, im.height, im.rmax);
+  return !ctx->opt.force_gang && !ctx->opt.generic_only && im.rmax > 0 &&
+         reg_kernel_ok(im.width, im.height, im.rmax);
 }
 
 int gang_size(const hasf_ctx* ctx, const hasf_image& im) {
@@ -252,8 +264,9 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
     j.h = im.height;
     j.pitch = im.pitch;
     j.wpr = words_per_row(im.width);
+    j.stable = (op == OP_HASF && im.rmax < 0) ? 1 : 0;
     j.r_lo = (op == OP_HASF) ? 1 : im.rmax;
-    j.r_hi = im.rmax;
+    j.r_hi = im.rmax < 0 ? -im.rmax : im.rmax;
     j.op = op;
     j.conn = im.connectivity;
     j.plane_words = plane_words(im.width, im.height);
@@ -263,6 +276,10 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
     const size_t gwords = (size_t)im.height * j.wpr;
     j.g0 = base ? (uint32_t*)(base + off) : nullptr;
     off += align_up(gwords * 4);
+    if (j.stable) {
+      j.g1 = base ? (uint32_t*)(base + off) : nullptr;
+      off += align_up(gwords * 4);
+    }
     const bool need_c = (op == OP_THICK) || im.C != nullptr;
     if (need_c) {
       j.cp = base ? (uint32_t*)(base + off) : nullptr;
@@ -305,8 +322,8 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
   // Largest work first (the paper's scheduler bound: a worker never holds
   // more than its share of the largest tasks).
   auto by_work = [&](int a, int b) {
-    const long long wa = (long long)imgs[a].width * imgs[a].height * imgs[a].rmax;
-    const long long wb = (long long)imgs[b].width * imgs[b].height * imgs[b].rmax;
+    const long long wa = (long long)imgs[a].width * imgs[a].height * std::abs(imgs[a].rmax);
+    const long long wb = (long long)imgs[b].width * imgs[b].height * std::abs(imgs[b].rmax);
     return wa > wb;
   };
   std::stable_sort(p.order.begin(), p.order.end(), by_work);
@@ -529,7 +546,7 @@ void retire_finished(hasf_ctx* ctx) {  // ctx->mu held
       if (f) {
         b.reported[k] = 1;
         const int st = f - 1;
-        ctx->finished[b.tickets[k]] = st == DEV_TIMEOUT ? HASF_ETIMEOUT : st;
+        ctx->finished[b.tickets[k]] = public_status(st);
         ctx->launched.erase(b.tickets[k]);
         ctx->cv.notify_all();
       }
@@ -542,8 +559,7 @@ void retire_finished(hasf_ctx* ctx) {  // ctx->mu held
     for (size_t k = 0; k < b.tickets.size(); ++k) {
       if (b.reported[k]) continue;
       const int f = *(volatile int*)(b.h_status + k);
-      const int st = (q == cudaSuccess && f) ? f - 1 : HASF_ECUDA;
-      ctx->finished[b.tickets[k]] = st == DEV_TIMEOUT ? HASF_ETIMEOUT : st;
+      ctx->finished[b.tickets[k]] = (q == cudaSuccess && f) ? public_status(f - 1) : HASF_ECUDA;
       ctx->launched.erase(b.tickets[k]);
     }
     if (q != cudaSuccess) cudaGetLastError();
@@ -790,7 +806,7 @@ int hasf_smooth_batch(hasf_ctx* ctx, const hasf_image* imgs, int n, void* stream
 }
 
 int hasf_operator(hasf_ctx* ctx, int op, const hasf_image* img, void* stream) {
-  if (!ctx || !img || op < OP_THIN || op > OP_HF) return HASF_EINVAL;
+  if (!ctx || !img || op < OP_THIN || op > OP_HF || img->rmax < 1) return HASF_EINVAL;
   return run_images(ctx, img, 1, op, (cudaStream_t)stream);
 }
 
@@ -803,7 +819,7 @@ int hasf_status_of(hasf_ctx* ctx, void* stream) {
   e = cudaMemcpy(&st, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_status(e);
-  return st == DEV_TIMEOUT ? HASF_ETIMEOUT : (st ? HASF_ECUDA : HASF_OK);
+  return public_status(st);
 }
 
 namespace {
@@ -1218,6 +1234,7 @@ const char* hasf_strerror(int status) {
     case HASF_EBUDGET: return "job exceeds the context's memory budget";
     case HASF_EPENDING: return "job not finished";
     case HASF_ETIMEOUT: return "device iteration cap or wait deadline reached";
+    case HASF_EUNSTABLE: return "run to stability: the last allowed step still changed the image";
     case HASF_ECUDA: return "CUDA runtime error";
     case HASF_ENOTFOUND: return "unknown ticket";
     case HASF_ECANCELLED: return "job cancelled";

@@ -502,17 +502,39 @@ __device__ __forceinline__ void job_done(const Job& jb, int gang) {
   }
 }
 
+// Whether the current set differs anywhere from the plane g (h * wpr words);
+// the same answer on every thread of the job.
+template <class Mode>
+__device__ int differs(Ctx<Mode>& k, const uint32_t* g) {
+  const int total = k.h * k.wpr;
+  int d = 0;
+  for (int t = k.gtid; t < total; t += k.gthreads) {
+    const int y = t / k.wpr, j = t - y * k.wpr;
+    d |= Mode::ld(k.S + k.idx(y, j)) != Mode::ld(g + t);
+  }
+  return k.m.sync_or(d);
+}
+
 template <class Mode, int CONN>
 __device__ void run_job(Ctx<Mode>& k, const Job& jb, uint32_t* planes_base) {
   load_job(k, jb, planes_base);
   bool ok = true;
   switch (jb.op) {
-    case OP_HASF:
+    case OP_HASF: {
+      // run to stability: stop after the first step that changes nothing
+      bool fixed = false;
       for (int r = jb.r_lo; ok && r <= jb.r_hi; ++r) {
+        if (jb.stable) snapshot(k, jb.g1);
         ok = run_hc<Mode, CONN>(k, jb, r);
         if (ok) ok = run_hf<Mode, CONN>(k, jb, r);
+        if (ok && jb.stable && !differs(k, jb.g1)) {
+          fixed = true;
+          break;
+        }
       }
+      if (ok && jb.stable && !fixed && threadIdx.x == 0) atomicMax(jb.status, (int)DEV_UNSTABLE);
       break;
+    }
     case OP_THIN: ok = run_operator<Mode, CONN>(k, jb.r_hi, true, nullptr, jb.cp); break;
     case OP_THICK: ok = run_operator<Mode, CONN>(k, jb.r_hi, false, jb.cp, nullptr); break;
     case OP_HC: ok = run_hc<Mode, CONN>(k, jb, jb.r_hi); break;

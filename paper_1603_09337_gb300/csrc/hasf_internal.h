@@ -32,7 +32,9 @@ enum StatIndex : int {
 };
 
 // Device status codes written by kernels (a subset of hasf_status).
-enum DevStatus : int { DEV_OK = 0, DEV_TIMEOUT = 5 };
+// Device status of a job; jobs of one launch combine theirs with atomicMax,
+// so the more serious status wins.
+enum DevStatus : int { DEV_OK = 0, DEV_UNSTABLE = 1, DEV_TIMEOUT = 5 };
 
 // One image job as the kernels see it.  Planes are bit-packed, 32 pixels per
 // 32-bit word, bit b of word j of row y = pixel (32 j + b, y).
@@ -44,6 +46,7 @@ struct Job {
   uint32_t* g0;      // h * wpr words: snapshot of the operator input
   uint32_t* cp;      // h * wpr words or null: kept points (C cap X) / W / V
   uint32_t* dp;      // h * wpr words or null: forbidden points (D minus X)
+  uint32_t* g1;      // run to stability: h * wpr words, the image before the step
   uint32_t* planes;  // gang mode: 3 padded planes (S, F, cand); else null
   unsigned* sync;    // gang mode: 8 barrier words; else null
   int* status;       // device status word of the job
@@ -56,7 +59,7 @@ struct Job {
   int gang;          // CTAs cooperating on the job (gang mode)
   int cap;           // rounds allowed per level before DEV_TIMEOUT
   int plane_words;   // words per padded plane (see plane_words())
-  int pad_;
+  int stable;        // 1: stop after the first step r that changes nothing
 };
 
 // Padded plane geometry shared by both modes: rows -1..h, P words per row

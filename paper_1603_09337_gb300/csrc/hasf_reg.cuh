@@ -34,7 +34,7 @@ constexpr int kRegPitch = kRegW + 1;                    // M and cand row pitch
 constexpr int kRegPadR = 31;  // zero rows above and below the F plane (rmax <= 31)
 
 __host__ __device__ inline bool reg_kernel_fits(int w, int h, int rmax) {
-  return w <= 32 * kRegW && h <= kRegRows && rmax <= kRegPadR;
+  return w <= 32 * kRegW && h <= kRegRows && rmax >= 1 && rmax <= kRegPadR;
 }
 // F plane of the register kernel: rows -kRegPadR .. h + kRegPadR - 1, row pitch
 // row_pitch(w) (the last word of every row is zero), plus one leading word.

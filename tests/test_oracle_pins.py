@@ -339,3 +339,59 @@ def test_hasf_trivial_cases():
 def test_rmax_zero_is_identity():
     X = synth.shapes_image(3, 30, 20, 3, 3, 8)
     np.testing.assert_array_equal(oracle.hasf(X, 0), X)
+
+
+# ---- run to stability (the unbounded radius of Table 1, read as "until a step
+# changes nothing") ----------------------------------------------------------
+
+def test_stable_stops_at_once_on_an_open_and_closed_image():
+    """Separated large discs left unchanged by the opening and the closing by
+    B_1 are a fixed point of step 1, so the run stops there with X itself."""
+    used = 0
+    for seed in range(12):
+        rng = synth.SplitMix64(seed + 4000)
+        X = np.zeros((96, 96), np.uint8)
+        for cx, cy in [(24, 24), (72, 24), (24, 72), (72, 72)]:
+            rad = rng.randint(9, 16)
+            synth._paint_ellipse(X, cx + rng.randint(-3, 3), cy + rng.randint(-3, 3),
+                                 rad, rad, 1, 0, 1)
+        if not ((B.opening(X, 1) == X).all() and (B.closing(X, 1) == X).all()):
+            continue
+        used += 1
+        out, r = oracle.hasf_stable(X, 64)
+        assert r == 1
+        np.testing.assert_array_equal(out, X)
+    assert used >= 3
+
+
+@pytest.mark.parametrize("conn", [8, 4])
+def test_stable_stops_at_the_first_step_that_changes_nothing(conn):
+    """The run's radius r is the first one whose step leaves the image as it
+    was: HASF_r(X) = HASF_{r-1}(X) and HASF_s(X) != HASF_{s-1}(X) for s < r;
+    the output is HASF_r(X)."""
+    seen = 0
+    for seed in range(6):
+        X = synth.shapes_image(seed + 900, 56, 48, 4, 4, 12, n_holes=2, hole_lo=2, hole_hi=4,
+                               jitter=1, noise_permille=40)
+        C = synth.constraint_points(seed, X, 6)
+        out, r = oracle.hasf_stable(X, 16, C=C, conn=conn)
+        assert r >= 1
+        seen += r > 1
+        prev = (X != 0).astype(np.uint8)
+        for s in range(1, r + 1):
+            cur = oracle.hasf(X, s, C=C, conn=conn)
+            assert (s == r) == bool((cur == prev).all()), f"seed {seed} step {s}"
+            prev = cur
+        np.testing.assert_array_equal(out, prev)
+    assert seen >= 3
+
+
+def test_stable_reports_the_cap():
+    """A run capped before its fixed point returns 0 and HASF_cap(X)."""
+    X = synth.shapes_image(931, 56, 48, 4, 4, 12, n_holes=2, hole_lo=2, hole_hi=4, jitter=1,
+                           noise_permille=40)
+    out_full, r = oracle.hasf_stable(X, 16)
+    assert r >= 2
+    out, r1 = oracle.hasf_stable(X, r - 1)
+    assert r1 == 0
+    np.testing.assert_array_equal(out, oracle.hasf(X, r - 1))
