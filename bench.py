@@ -129,9 +129,13 @@ def _oracle_job(args):
     import oracle
     X, C, rmax = args[:3]
     conn = args[3] if len(args) > 3 else 8
+    st = oracle.Stats()
     t = time.perf_counter()
-    oracle.hasf(X, rmax, C=C, conn=conn)
-    return time.perf_counter() - t
+    oracle.hasf(X, rmax, C=C, conn=conn, stats=st)
+    dt = time.perf_counter() - t
+    # the sequential method's work: 9 simple tests per changed point plus
+    # 4 * rmax EDTs of N points
+    return dt, 9 * st.changes + 4 * rmax * X.size
 
 
 def _pool(cores):
@@ -144,11 +148,12 @@ def _pool(cores):
 def cpu_oracle_rate(jobs, cores):
     """Images/s of the oracle on `cores` host processes over `jobs`."""
     with _pool(cores) as pool:
-        pool.map(_oracle_job, [(jobs[0].X, jobs[0].C, jobs[0].rmax)] * cores)  # warm workers
+        pool.map(_oracle_job, [(jobs[0].X, jobs[0].C, jobs[0].rmax, jobs[0].conn)] * cores)
         t0 = time.perf_counter()
         per = pool.map(_oracle_job, [(j.X, j.C, j.rmax, j.conn) for j in jobs], chunksize=1)
         wall = time.perf_counter() - t0
-    return len(jobs) / wall, wall, sum(per)
+    cpu_oracle_rate.seq_ops_per_image = sum(p[1] for p in per) / max(1, len(per))
+    return len(jobs) / wall, wall, sum(p[0] for p in per)
 
 
 def run_reference(args):
@@ -466,7 +471,8 @@ def run_hasf(args):
         rate, cwall, cwork = cpu_oracle_rate(sample, cores)
         cpu = {"value": rate, "unit": "images/s", "cores": cores, "kind": "oracle",
                "sample": f"{len(sample)} images of the workload (other seeds), one oracle "
-                         f"process per core, {cwork:.1f} s of CPU work in {cwall:.1f} s"}
+                         f"process per core, {cwork:.1f} s of CPU work in {cwall:.1f} s",
+               "sequential_method_ops_per_image": cpu_oracle_rate.seq_ops_per_image}
     elif not args.no_cpu and ws == 1:
         # One full image takes the oracle minutes: time a 1024 x 1024 window of
         # it instead and scale by pixels (the work per pixel of a window is
