@@ -1,13 +1,14 @@
 """CPU oracle for the homotopic alternating sequential filter (HASF).
 
-TEST INFRASTRUCTURE ONLY.  The plain single-threaded C program in
-``hasf_oracle.c`` restates what the method of Mahmoudi & Akil (arXiv
+TEST INFRASTRUCTURE ONLY.  The plain single-threaded C programs in
+``hasf_oracle.c`` and ``hasf3d_oracle.c`` restate what the method of Mahmoudi & Akil (arXiv
 1603.09337) computes; this module compiles it with gcc and wraps it with
 ctypes and numpy.  Only the test suite, the smoke check and the CPU-baseline
 leg of the benchmark may import it.  The CUDA library never does, and the two
 share no code.
 
-Every wrapper takes and returns numpy arrays of shape (h, w).
+Every 2D wrapper takes and returns numpy arrays of shape (h, w); the 3D ones
+(``*3d``, in ``hasf3d_oracle.c``) arrays of shape (d, h, w).
 """
 from __future__ import annotations
 
@@ -19,7 +20,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "hasf_oracle.c")
+_SRCS = [os.path.join(_HERE, "hasf_oracle.c"), os.path.join(_HERE, "hasf3d_oracle.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libhasf_oracle.so")
 
@@ -44,11 +45,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/libhasf_oracle.so``."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     stale = (not os.path.exists(_LIB_PATH)
-             or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC))
+             or os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(f) for f in _SRCS))
     if force or stale:
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-Wall", "-Wextra",
-                        "-o", tmp, _SRC], check=True)
+                        "-o", tmp, *_SRCS], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -73,10 +74,15 @@ def load():
             lib.hasf_oracle_hf.argtypes = [u8p, u8p, ci, ci, ci, ci, sp]
             lib.hasf_oracle_hasf.argtypes = [u8p, u8p, u8p, ci, ci, ci, ci, u8p, sp]
             lib.hasf_oracle_hasf_stable.argtypes = [u8p, u8p, u8p, ci, ci, ci, ci, u8p, sp]
+            lib.hasf3d_oracle_simple.argtypes = [ctypes.c_uint32]
+            lib.hasf3d_oracle_edt.argtypes = [u8p, ci, ci, ci, ci, ci, i64p]
+            lib.hasf3d_oracle_hasf.argtypes = [u8p, u8p, u8p, ci, ci, ci, ci, u8p]
+            lib.hasf3d_oracle_operator.argtypes = [u8p, u8p, ci, ci, ci, ci, ci]
             for name in ("hasf_oracle_simple_lut", "hasf_oracle_edt", "hasf_oracle_dilate",
                          "hasf_oracle_erode", "hasf_oracle_thin", "hasf_oracle_thicken",
                          "hasf_oracle_hc", "hasf_oracle_hf", "hasf_oracle_hasf",
-                         "hasf_oracle_hasf_stable"):
+                         "hasf_oracle_hasf_stable", "hasf3d_oracle_simple", "hasf3d_oracle_edt",
+                         "hasf3d_oracle_hasf", "hasf3d_oracle_operator"):
                 getattr(lib, name).restype = ci
             lib.hasf_oracle_stats_size.restype = ci
             assert lib.hasf_oracle_stats_size() == ctypes.sizeof(Stats)
@@ -214,4 +220,46 @@ def hasf_stable(X, rcap: int = 64, C=None, D=None, conn: int = 8,
     if r < 0:
         raise ValueError("hasf_stable: bad arguments")
     return out, r
+
+
+# ---- 3D: (26, 6) adjacency, volumes indexed [z, y, x] --------------------------
+
+def simple3d(code: int) -> bool:
+    """Simplicity of the centre of a 3 x 3 x 3 neighbourhood; bit
+    (dz+1)*9 + (dy+1)*3 + (dx+1) of code = object (the centre bit is ignored)."""
+    return bool(load().hasf3d_oracle_simple(code & 0x7FFFFFF))
+
+
+def edt3d(feat, r: int, outside_is_feature: bool = False) -> np.ndarray:
+    """Squared distance to the nearest feature voxel, clamped at r^2 + 1."""
+    f = _u8(feat)
+    d, h, w = f.shape
+    out = np.zeros(f.shape, np.int64)
+    _check(load().hasf3d_oracle_edt(_p(f, ctypes.c_uint8), w, h, d, int(outside_is_feature), r,
+                                    _p(out, ctypes.c_int64)), "edt3d")
+    return out
+
+
+def operator3d(S, K, r: int, thin: bool) -> np.ndarray:
+    """H(S, K) (thin) or *H(S, K) in 3D with the clamped priority of radius r."""
+    s = _u8(S).copy()
+    k = _u8(K)
+    d, h, w = s.shape
+    _check(load().hasf3d_oracle_operator(_p(s, ctypes.c_uint8), _p(k, ctypes.c_uint8), w, h, d,
+                                         r, int(thin)), "operator3d")
+    return s
+
+
+def hasf3d(X, rmax: int, C=None, D=None) -> np.ndarray:
+    """HASF_rmax^{C,D} of a volume X (d, h, w) with (26, 6) adjacency."""
+    x = _u8(X)
+    d, h, w = x.shape
+    c = _u8(C) if C is not None else None
+    dd = _u8(D) if D is not None else None
+    out = np.zeros_like(x)
+    _check(load().hasf3d_oracle_hasf(_p(x, ctypes.c_uint8),
+                                     _p(c, ctypes.c_uint8) if c is not None else None,
+                                     _p(dd, ctypes.c_uint8) if dd is not None else None,
+                                     w, h, d, rmax, _p(out, ctypes.c_uint8)), "hasf3d")
+    return out
 
