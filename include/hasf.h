@@ -226,6 +226,37 @@ int hasf_autotune(hasf_ctx *ctx, int32_t width, int32_t height, int32_t rmax,
 int hasf_tuning_save(hasf_ctx *ctx, const char *path);
 int hasf_tuning_load(hasf_ctx *ctx, const char *path);
 
+/* ---- Volumes ---------------------------------------------------------------- */
+
+/* One volume for the 3D filter: dense w x h x d bytes, x fastest (voxel
+ * (x, y, z) at in[(z * height + y) * width + x]), non-zero = object; C, D
+ * (same layout, may be NULL) as in hasf_image.  width, height, depth in
+ * [1, 4096] with at most 2^31 voxels; rmax in [1, 12]. */
+typedef struct hasf_volume {
+    const uint8_t *in;
+    uint8_t *out;         /* may equal in */
+    const uint8_t *C;
+    const uint8_t *D;
+    int32_t width;
+    int32_t height;
+    int32_t depth;
+    int32_t rmax;
+    int32_t reserved[2];  /* must be 0 */
+} hasf_volume;
+
+/* HASF_rmax^{C,D} of n volumes (device pointers), asynchronously on `stream`.
+ * The paper states the filter for 2D images and notes (Sec. 1) that it
+ * carries over to 3D; this is that extension with (26, 6) adjacency: a voxel
+ * is simple when its object 26-neighbours form one 26-connected component and
+ * the background voxels of its 18-neighbourhood 6-connected to a face
+ * neighbour form one 6-connected component; B_r is the ball |v|^2 <= r^2; the
+ * sweep order is levels, then rounds of the eight subfields (x, y, z mod 2)
+ * in the order s = 0..7 with parities (s & 1, (s >> 1) & 1, s >> 2).  Each
+ * volume is processed by a gang of CTAs; the library owns the scratch (seven
+ * bit planes per volume).  Errors as hasf_smooth_batch; a device-side
+ * HASF_ETIMEOUT is reported by hasf_status_of. */
+int hasf_smooth3d(hasf_ctx *ctx, const hasf_volume *vols, int n, void *stream);
+
 /* ---- Single operators (the same kernels, one step of the filter) --------- */
 
 /* Exact squared Euclidean distance transform (Sec. 4.1, Meijster's two

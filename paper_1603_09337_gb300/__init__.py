@@ -233,6 +233,26 @@ class Context:
         check(self.lib.hasf_smooth_host(self.h, arr, len(jobs)), "hasf_smooth_host")
 
     # -- serving ------------------------------------------------------------------
+    def smooth3d(self, volumes, stream=None):
+        """HASF of 3D volumes, (26, 6) adjacency.  volumes: list of
+        (X, rmax, C, D) with X a contiguous (d, h, w) uint8 CUDA tensor (C, D of
+        the same shape or None).  Returns the output tensors."""
+        import torch
+        arr = (_lib.HasfVolume * max(1, len(volumes)))()
+        outs = []
+        for i, (X, rmax, C, D) in enumerate(volumes):
+            if X.dim() != 3 or not X.is_contiguous() or X.dtype != torch.uint8:
+                raise ValueError("a volume is a contiguous (d, h, w) uint8 tensor")
+            out = torch.empty_like(X)
+            outs.append(out)
+            d, h, w = X.shape
+            arr[i] = _lib.HasfVolume(X.data_ptr(), out.data_ptr(),
+                                     None if C is None else C.data_ptr(),
+                                     None if D is None else D.data_ptr(), w, h, d, rmax, (0, 0))
+        check(self.lib.hasf_smooth3d(self.h, arr, len(volumes), _stream_handle(stream)),
+              "hasf_smooth3d")
+        return outs
+
     def submit(self, X, rmax: int, out, C=None, D=None, conn: int = 8) -> int:
         d = _desc(X, out, C, D, rmax, conn)
         t = ctypes.c_uint64()

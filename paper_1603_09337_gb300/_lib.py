@@ -33,7 +33,7 @@ EXPORTS = (
     "hasf_set_option", "hasf_strerror", "hasf_edt", "hasf_operator", "hasf_simple_table",
     "hasf_levels", "hasf_read_stats", "hasf_smooth_noalloc", "hasf_graph_create",
     "hasf_graph_launch", "hasf_graph_destroy", "hasf_autotune", "hasf_tuning_save",
-    "hasf_tuning_load",
+    "hasf_tuning_load", "hasf_smooth3d",
 )
 
 
@@ -49,6 +49,20 @@ class HasfImage(ctypes.Structure):
         ("rmax", ctypes.c_int32),
         ("connectivity", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+    ]
+
+
+class HasfVolume(ctypes.Structure):
+    _fields_ = [
+        ("in_", ctypes.c_void_p),
+        ("out", ctypes.c_void_p),
+        ("C", ctypes.c_void_p),
+        ("D", ctypes.c_void_p),
+        ("width", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("depth", ctypes.c_int32),
+        ("rmax", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -93,6 +107,7 @@ def _declare(lib):
     lib.hasf_autotune.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(i32)]
     lib.hasf_tuning_save.argtypes = [vp, ctypes.c_char_p]
     lib.hasf_tuning_load.argtypes = [vp, ctypes.c_char_p]
+    lib.hasf_smooth3d.argtypes = [vp, ctypes.POINTER(HasfVolume), ci, vp]
     for name in EXPORTS:
         if name != "hasf_strerror":
             getattr(lib, name).restype = ci

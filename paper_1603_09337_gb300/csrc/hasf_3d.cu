@@ -1,0 +1,373 @@
+// hasf_3d.cu -- HASF of 3D volumes with (26, 6) adjacency.
+//
+// The paper states the filter for 2D images and notes (Sec. 1) that it
+// applies to 3D ones.  Here the same scheme runs on volumes: eqs. (i) and (ii)
+// with B_r the ball |v|^2 <= r^2; priorities in threshold form (a voxel has
+// priority <= l iff a feature voxel lies at a lattice vector of squared norm
+// <= l; the levels are the sums of three squares); rounds of the eight
+// subfields (x mod 2, y mod 2, z mod 2), taken in the order s = 0..7 with
+// parities (s & 1, (s >> 1) & 1, s >> 2).  Voxels of one subfield differ by an
+// even amount in every coordinate, so they are never 26-adjacent and a whole
+// subfield is updated at once.
+//
+// Simple voxels: the object voxels of the 26-neighbourhood form one
+// 26-connected component and the background voxels of the 18-neighbourhood
+// that are 6-connected to a face neighbour form one 6-connected component.
+// Both numbers are computed on the 27-bit neighbourhood code by flood fill
+// with mask dilations (shifts by 1, 3, 9 for x, y, z).
+//
+// Layout: each plane is d * h rows of ceil(w / 32) words (bit b of word j of
+// row (y, z) = voxel (32 j + b, y, z)), in global memory (L2).  A volume is
+// processed by a gang of co-resident CTAs meeting at the bounded gang barrier
+// after every phase.
+#include <cstdint>
+#include <algorithm>
+#include <mutex>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "hasf_device.cuh"
+
+namespace hasf {
+
+constexpr int kMaxR3 = kMaxR3D;
+constexpr int kMaxOff3 = 7300;   // lattice vectors with 0 < |v|^2 <= 144
+constexpr int kMaxLev3 = 150;
+
+struct LevelTable3 {
+  uint16_t value[kMaxLev3];
+  uint16_t start[kMaxLev3 + 1];
+  uint16_t nlev[kMaxR3 + 1];
+  int8_t off[kMaxOff3][3];
+};
+static __constant__ LevelTable3 c_lv3;
+
+// ---------------------------------------------------------------------------
+// Topology of a 3 x 3 x 3 neighbourhood.  Position of offset (dx, dy, dz):
+// (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); the centre is position 13.
+// ---------------------------------------------------------------------------
+
+constexpr uint32_t cube_mask(int axis, int val) {
+  uint32_t m = 0;
+  for (int i = 0; i < 27; ++i) {
+    const int c = axis == 0 ? i % 3 : (axis == 1 ? (i / 3) % 3 : i / 9);
+    if (c == val) m |= 1u << i;
+  }
+  return m;
+}
+constexpr uint32_t l1_mask(int lo, int hi) {
+  uint32_t m = 0;
+  for (int i = 0; i < 27; ++i) {
+    const int a = i % 3 - 1, b = (i / 3) % 3 - 1, c = i / 9 - 1;
+    const int l1 = (a < 0 ? -a : a) + (b < 0 ? -b : b) + (c < 0 ? -c : c);
+    if (l1 >= lo && l1 <= hi) m |= 1u << i;
+  }
+  return m;
+}
+constexpr uint32_t kX0 = cube_mask(0, 0), kX2 = cube_mask(0, 2);
+constexpr uint32_t kY0 = cube_mask(1, 0), kY2 = cube_mask(1, 2);
+constexpr uint32_t kZ0 = cube_mask(2, 0), kZ2 = cube_mask(2, 2);
+constexpr uint32_t kN26 = l1_mask(1, 3), kN18 = l1_mask(1, 2), kN6 = l1_mask(1, 1);
+
+__device__ __forceinline__ uint32_t dil_x(uint32_t s) {
+  return s | ((s & ~kX2) << 1) | ((s & ~kX0) >> 1);
+}
+__device__ __forceinline__ uint32_t dil_y(uint32_t s) {
+  return s | ((s & ~kY2) << 3) | ((s & ~kY0) >> 3);
+}
+__device__ __forceinline__ uint32_t dil_z(uint32_t s) {
+  return s | ((s & ~kZ2) << 9) | ((s & ~kZ0) >> 9);
+}
+
+__device__ __forceinline__ bool simple3(uint32_t code) {
+  // one 26-component of object neighbours
+  const uint32_t obj = code & kN26;
+  if (!obj) return false;
+  uint32_t comp = obj & (0u - obj);
+  for (int it = 0; it < 27; ++it) {
+    const uint32_t nc = dil_z(dil_y(dil_x(comp))) & obj;
+    if (nc == comp) break;
+    comp = nc;
+  }
+  if (comp != obj) return false;
+  // one 6-component of 18-neighbourhood background touching a face neighbour
+  const uint32_t bg = ~code & kN18;
+  const uint32_t touch = bg & kN6;
+  if (!touch) return false;
+  comp = touch & (0u - touch);
+  for (int it = 0; it < 27; ++it) {
+    const uint32_t nc = (dil_x(comp) | dil_y(comp) | dil_z(comp)) & bg;
+    if (nc == comp) break;
+    comp = nc;
+  }
+  return (touch & ~comp) == 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Per-CTA view of a volume job.
+// ---------------------------------------------------------------------------
+
+struct V3 {
+  int w, h, d, wpr;
+  long long nw;        // words per plane
+  int gtid, gthreads;  // this thread in the gang
+  bool solo;
+  GangMode gm;
+  uint32_t lastmask;
+  unsigned long long n_tests, n_ring, n_rounds, n_levels;
+  __device__ __forceinline__ int bar(int v) { return solo ? __syncthreads_or(v) : gm.barrier(v); }
+  __device__ __forceinline__ bool failed() const { return !solo && gm.failed(); }
+  __device__ __forceinline__ uint32_t rowmask(int j) const {
+    return j == wpr - 1 ? lastmask : 0xFFFFFFFFu;
+  }
+  __device__ __forceinline__ uint32_t ld(const uint32_t* P, int j, int y, int z) const {
+    if (j < 0 || j >= wpr || y < 0 || y >= h || z < 0 || z >= d) return 0u;
+    return __ldcg(P + ((long long)z * h + y) * wpr + j);
+  }
+};
+
+__device__ __forceinline__ void word_pos(const V3& v, long long t, int& j, int& y, int& z) {
+  j = (int)(t % v.wpr);
+  const long long row = t / v.wpr;
+  y = (int)(row % v.h);
+  z = (int)(row / v.h);
+}
+
+__device__ uint32_t pack3(const uint8_t* p, int n) {
+  uint32_t s = 0;
+  for (int b = 0; b < n; ++b) s |= (p[b] != 0 ? 1u : 0u) << b;
+  return s;
+}
+
+// One constrained thinning (thin) or thickening of S at radius r; the points
+// allowed to change lie in pos (if given) and not in neg (if given).
+__device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos,
+                    const uint32_t* neg) {
+  for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
+    const uint32_t s = __ldcg(jb.S + t);
+    __stcg(jb.F + t, s);
+    uint32_t m = v.rowmask((int)(t % v.wpr));
+    if (pos) m &= __ldcg(pos + t);
+    if (neg) m &= ~__ldcg(neg + t);
+    __stcg(jb.M + t, m);
+    __stcg(jb.cand + t, 0u);
+  }
+  v.bar(0);
+  if (v.failed()) return false;
+  const int nlev = c_lv3.nlev[r];
+  for (int li = 0; li < nlev; ++li) {
+    // new candidates: points whose priority is the level's value
+    int any = 0;
+    const int o0 = c_lv3.start[li], o1 = c_lv3.start[li + 1];
+    for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
+      const uint32_t s = __ldcg(jb.S + t), c = __ldcg(jb.cand + t);
+      const uint32_t pend = __ldcg(jb.M + t) & (thin ? s : ~s) & ~c;
+      if (!pend) continue;
+      int j, y, z;
+      word_pos(v, t, j, y, z);
+      uint32_t acc = thin ? 0xFFFFFFFFu : 0u;
+      for (int o = o0; o < o1; ++o) {
+        const int dx = c_lv3.off[o][0], dy = c_lv3.off[o][1], dz = c_lv3.off[o][2];
+        const int j0 = j + (dx >> 5), sh = dx & 31;
+        const uint32_t lo = v.ld(jb.F, j0, y + dy, z + dz);
+        const uint32_t val = sh ? __funnelshift_r(lo, v.ld(jb.F, j0 + 1, y + dy, z + dz), sh) : lo;
+        acc = thin ? (acc & val) : (acc | val);
+        ++v.n_ring;
+        if (((o - o0) & 3) == 3 && !(pend & (thin ? acc : ~acc))) break;
+      }
+      const uint32_t add = pend & (thin ? ~acc : acc);
+      if (add) {
+        __stcg(jb.cand + t, c | add);
+        any = 1;
+      }
+    }
+    any = v.bar(any);
+    if (v.failed()) return false;
+    if (!any) continue;
+    ++v.n_levels;
+    // rounds of the eight subfields until a round changes nothing
+    for (int round = 0;; ++round) {
+      if (round >= jb.cap) return false;
+      ++v.n_rounds;
+      int changed = 0;
+      for (int sub = 0; sub < 8; ++sub) {
+        const int sx = sub & 1, sy = (sub >> 1) & 1, sz = sub >> 2;
+        const int ny = (v.h - sy + 1) >> 1, nz = (v.d - sz + 1) >> 1;
+        const long long nsub = (long long)ny * nz * v.wpr;
+        const uint32_t xm = sx ? 0xAAAAAAAAu : 0x55555555u;
+        for (long long q = v.gtid; q < nsub; q += v.gthreads) {
+          const int j = (int)(q % v.wpr);
+          const long long rr = q / v.wpr;
+          const int y = sy + 2 * (int)(rr % ny), z = sz + 2 * (int)(rr / ny);
+          const long long t = ((long long)z * v.h + y) * v.wpr + j;
+          const uint32_t call = __ldcg(jb.cand + t);
+          uint32_t cw = call & xm;
+          if (!cw) continue;
+          // the 3 x 3 rows around (y, z), three words each
+          uint64_t win[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const int dy = k % 3 - 1, dz = k / 3 - 1;
+            const uint32_t p = v.ld(jb.S, j - 1, y + dy, z + dz);
+            const uint32_t c = v.ld(jb.S, j, y + dy, z + dz);
+            const uint32_t n = v.ld(jb.S, j + 1, y + dy, z + dz);
+            win[k] = ((uint64_t)n << 33) | ((uint64_t)c << 1) | (uint64_t)(p >> 31);
+          }
+          const uint32_t cur = (uint32_t)(win[4] >> 1);
+          uint32_t chg = 0;
+          while (cw) {
+            const int b = __ffs(cw) - 1;
+            cw &= cw - 1u;
+            uint32_t code = 0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) code |= (uint32_t)((win[k] >> b) & 7u) << (3 * k);
+            ++v.n_tests;
+            if (simple3(code)) chg |= 1u << b;
+          }
+          if (chg) {
+            __stcg(jb.S + t, thin ? (cur & ~chg) : (cur | chg));
+            __stcg(jb.cand + t, call & ~chg);
+            changed = 1;
+          }
+        }
+        const int o = v.bar(sub == 7 ? changed : 0);
+        if (v.failed()) return false;
+        if (sub == 7) changed = o;
+      }
+      if (!changed) break;
+    }
+  }
+  return true;
+}
+
+__device__ void snapshot3(V3& v, const Job3& jb) {
+  for (long long t = v.gtid; t < v.nw; t += v.gthreads) __stcg(jb.g0 + t, __ldcg(jb.S + t));
+  v.bar(0);
+}
+
+// CTA b works on part ctamap[b].y of job ctamap[b].x (a gang of jobs[].gang CTAs).
+__global__ void __launch_bounds__(kThreads, 1)
+hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
+  __shared__ int flag;
+  const int2 m = ctamap[blockIdx.x];
+  const Job3& jb = jobs[m.x];
+  V3 v;
+  v.w = jb.w;
+  v.h = jb.h;
+  v.d = jb.d;
+  v.wpr = jb.wpr;
+  v.nw = (long long)jb.d * jb.h * jb.wpr;
+  v.gtid = m.y * blockDim.x + threadIdx.x;
+  v.gthreads = jb.gang * blockDim.x;
+  v.solo = jb.gang == 1;
+  v.gm.init(jb.sync, jb.gang, &flag);
+  const int rem = jb.w & 31;
+  v.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
+  v.n_tests = v.n_ring = v.n_rounds = v.n_levels = 0;
+  // pack X (and C cap X, D minus X)
+  for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
+    int j, y, z;
+    word_pos(v, t, j, y, z);
+    const long long off = ((long long)z * jb.h + y) * jb.w + 32LL * j;
+    const int n = min(32, jb.w - 32 * j);
+    const uint32_t x = pack3(jb.in + off, n);
+    __stcg(jb.S + t, x);
+    if (jb.cp) __stcg(jb.cp + t, jb.C ? (pack3(jb.C + off, n) & x) : 0u);
+    if (jb.dp) __stcg(jb.dp + t, jb.D ? (pack3(jb.D + off, n) & ~x) : 0u);
+  }
+  v.bar(0);
+  bool ok = !v.failed();
+  for (int r = 1; ok && r <= jb.rmax; ++r) {
+    snapshot3(v, jb);   // HC_r: thinning that keeps C, thickening inside its input
+    ok = op3(v, jb, r, true, nullptr, jb.cp) && op3(v, jb, r, false, jb.g0, nullptr);
+    if (!ok) break;
+    snapshot3(v, jb);   // HF_r: thickening that avoids D, thinning that keeps its input
+    ok = op3(v, jb, r, false, nullptr, jb.dp) && op3(v, jb, r, true, nullptr, jb.g0);
+  }
+  if (ok) {
+    for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
+      int j, y, z;
+      word_pos(v, t, j, y, z);
+      const uint32_t s = __ldcg(jb.S + t);
+      uint8_t* o = jb.out + ((long long)z * jb.h + y) * jb.w + 32LL * j;
+      const int n = min(32, jb.w - 32 * j);
+      for (int b = 0; b < n; ++b) o[b] = (uint8_t)((s >> b) & 1u);
+    }
+  } else if (threadIdx.x == 0) {
+    atomicMax(jb.status, (int)DEV_TIMEOUT);
+  }
+  if (jb.stats) {
+    unsigned long long a = v.n_tests, b = v.n_ring;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+      b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(jb.stats + STAT_WORD_TESTS, a);
+      atomicAdd(jb.stats + STAT_RING_EVALS, b);
+    }
+    if (v.gtid == 0) {
+      atomicAdd(jb.stats + STAT_LEVELS, v.n_levels);
+      atomicAdd(jb.stats + STAT_ROUNDS, v.n_rounds);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+
+cudaError_t upload_level_table_3d() {
+  static LevelTable3 tab;
+  static bool built = false;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!built) {
+    struct V { int n2, dx, dy, dz; };
+    std::vector<V> vs;
+    const int R = kMaxR3;
+    for (int dz = -R; dz <= R; ++dz)
+      for (int dy = -R; dy <= R; ++dy)
+        for (int dx = -R; dx <= R; ++dx) {
+          const int n2 = dx * dx + dy * dy + dz * dz;
+          if (n2 >= 1 && n2 <= R * R) vs.push_back({n2, dx, dy, dz});
+        }
+    std::stable_sort(vs.begin(), vs.end(), [](const V& a, const V& b) { return a.n2 < b.n2; });
+    if ((int)vs.size() > kMaxOff3) return cudaErrorInvalidValue;
+    int nl = 0;
+    for (size_t i = 0; i < vs.size(); ++i) {
+      if (i == 0 || vs[i].n2 != vs[i - 1].n2) {
+        if (nl >= kMaxLev3) return cudaErrorInvalidValue;
+        tab.value[nl] = (uint16_t)vs[i].n2;
+        tab.start[nl] = (uint16_t)i;
+        ++nl;
+      }
+      tab.off[i][0] = (int8_t)vs[i].dx;
+      tab.off[i][1] = (int8_t)vs[i].dy;
+      tab.off[i][2] = (int8_t)vs[i].dz;
+    }
+    tab.start[nl] = (uint16_t)vs.size();
+    for (int r = 0; r <= R; ++r) {
+      int c = 0;
+      while (c < nl && tab.value[c] <= r * r) ++c;
+      tab.nlev[r] = (uint16_t)c;
+    }
+    built = true;
+  }
+  return cudaMemcpyToSymbol(c_lv3, &tab, sizeof(tab));
+}
+
+int max_3d_ctas(int device) {
+  int per_sm = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hasf_3d_kernel, kThreads, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return per_sm * sms;
+}
+
+cudaError_t launch_3d(const Job3* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s) {
+  void* args[] = {(void*)&d_jobs, (void*)&d_ctamap};
+  return cudaLaunchCooperativeKernel((const void*)hasf_3d_kernel, dim3(nctas), dim3(kThreads),
+                                     args, 0, s);
+}
+
+}  // namespace hasf

@@ -120,6 +120,7 @@ struct hasf_ctx {
   int* d_status = nullptr;
   unsigned long long* d_stats = nullptr;  // STAT_COUNT counters
   unsigned long long launches = 0;        // kernel launches issued (host count)
+  int max3d = 1;                          // co-resident CTAs of the 3D kernel
 
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
@@ -698,6 +699,7 @@ int hasf_create(hasf_ctx** out, int device, size_t mem_budget_bytes) {
   e = cudaSetDevice(device);
   if (e != cudaSuccess) return cuda_status(e);
   e = upload_level_table();
+  if (e == cudaSuccess) e = upload_level_table_3d();
   if (e != cudaSuccess) return cuda_status(e);
   hasf_ctx* c = new (std::nothrow) hasf_ctx();
   if (!c) return HASF_ENOMEM;
@@ -707,6 +709,7 @@ int hasf_create(hasf_ctx** out, int device, size_t mem_budget_bytes) {
   c->max_smem = max_resident_smem(device);
   c->gang_max = std::max(1, max_gang_ctas(device));
   c->tile_gang_max = max_tile_gang_ctas(device);
+  c->max3d = std::max(1, max_3d_ctas(device));
   for (int l = 0; l < 8; ++l) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) c->lanes.push_back(st);
@@ -803,6 +806,116 @@ int hasf_smooth(hasf_ctx* ctx, const hasf_image* img, void* stream) {
 int hasf_smooth_batch(hasf_ctx* ctx, const hasf_image* imgs, int n, void* stream) {
   if (!ctx) return HASF_EINVAL;
   return run_images(ctx, imgs, n, OP_HASF, (cudaStream_t)stream);
+}
+
+// ---- 3D -------------------------------------------------------------------
+
+namespace {
+
+int validate3d(const hasf_volume* v) {
+  if (!v || !v->in || !v->out) return HASF_EINVAL;
+  if (v->width < 1 || v->height < 1 || v->depth < 1 || v->width > 4096 || v->height > 4096 ||
+      v->depth > 4096)
+    return HASF_EINVAL;
+  if ((long long)v->width * v->height * v->depth > (1LL << 31)) return HASF_EINVAL;
+  if (v->rmax < 1 || v->rmax > kMaxR3D) return HASF_EINVAL;
+  if (v->reserved[0] != 0 || v->reserved[1] != 0) return HASF_EINVAL;
+  return HASF_OK;
+}
+
+// Scratch of one volume: seven planes (S, F, cand, M, g0, C, D).
+size_t volume_bytes(const hasf_volume& v) {
+  const size_t nw = (size_t)v.depth * v.height * words_per_row(v.width);
+  return 7 * align_up(nw * 4);
+}
+
+int volume_gang(const hasf_ctx* ctx, const hasf_volume& v) {
+  const long long nw = (long long)v.depth * v.height * words_per_row(v.width);
+  long long g = (nw + 2047) / 2048;   // about 4 words per thread and pass
+  return (int)std::max(1LL, std::min(g, (long long)std::min(ctx->max3d, 64)));
+}
+
+}  // namespace
+
+int hasf_smooth3d(hasf_ctx* ctx, const hasf_volume* vols, int n, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && !vols)) return HASF_EINVAL;
+  for (int i = 0; i < n; ++i)
+    if (int v = validate3d(&vols[i])) return v;
+  if (n == 0) return HASF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_status(e);
+  int first = 0;
+  while (first < n) {
+    // a chunk: co-resident gangs within the budget
+    int cnt = 0, ctas = 0;
+    size_t bytes = 0;
+    while (first + cnt < n) {
+      const hasf_volume& v = vols[first + cnt];
+      const int g = volume_gang(ctx, v);
+      const size_t b = volume_bytes(v);
+      if (cnt > 0 && (ctas + g > ctx->max3d || bytes + b > ctx->budget / 2)) break;
+      ctas += g;
+      bytes += b;
+      ++cnt;
+    }
+    const size_t head = align_up(sizeof(Job3) * cnt) + align_up(sizeof(int2) * ctas) +
+                        align_up(sizeof(unsigned) * 8 * cnt);
+    if (head + bytes > ctx->budget) return HASF_EBUDGET;
+    int rc = ensure_arena(ctx, head + bytes, s);
+    if (rc) return rc;
+    char* base = (char*)ctx->arena;
+    std::vector<Job3> jobs(cnt);
+    std::vector<int2> map;
+    size_t off = head;
+    unsigned* d_sync = (unsigned*)(base + align_up(sizeof(Job3) * cnt) + align_up(sizeof(int2) * ctas));
+    for (int k = 0; k < cnt; ++k) {
+      const hasf_volume& v = vols[first + k];
+      Job3& j = jobs[k];
+      j = Job3{};
+      j.in = v.in;
+      j.out = v.out;
+      j.C = v.C;
+      j.D = v.D;
+      j.w = v.width;
+      j.h = v.height;
+      j.d = v.depth;
+      j.wpr = words_per_row(v.width);
+      j.rmax = v.rmax;
+      j.gang = volume_gang(ctx, v);
+      const long long vox = (long long)v.width * v.height * v.depth;
+      j.cap = ctx->opt.round_cap > 0 ? ctx->opt.round_cap : (int)std::min<long long>(vox + 2, INT_MAX);
+      const size_t pb = align_up((size_t)v.depth * v.height * j.wpr * 4);
+      uint32_t** planes[7] = {&j.S, &j.F, &j.cand, &j.M, &j.g0, &j.cp, &j.dp};
+      for (int q = 0; q < 7; ++q) {
+        *planes[q] = (uint32_t*)(base + off);
+        off += pb;
+      }
+      if (!v.C) j.cp = nullptr;
+      if (!v.D) j.dp = nullptr;
+      j.sync = d_sync + 8 * k;
+      j.status = ctx->d_status;
+      j.stats = ctx->opt.stats ? ctx->d_stats : nullptr;
+      for (int part = 0; part < j.gang; ++part) map.push_back(make_int2(k, part));
+    }
+    e = cudaMemcpyAsync(base, jobs.data(), sizeof(Job3) * cnt, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + align_up(sizeof(Job3) * cnt), map.data(), sizeof(int2) * ctas,
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_sync, 0, sizeof(unsigned) * 8 * cnt, s);
+    if (e == cudaSuccess)
+      e = launch_3d((const Job3*)base, (const int2*)(base + align_up(sizeof(Job3) * cnt)), ctas, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    ++ctx->launches;
+    first += cnt;
+    // the host vectors are copied from pageable memory (staged before return);
+    // the next chunk reuses the arena: wait for this one
+    if (first < n) {
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  return HASF_OK;
 }
 
 int hasf_operator(hasf_ctx* ctx, int op, const hasf_image* img, void* stream) {

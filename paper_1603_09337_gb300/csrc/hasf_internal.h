@@ -62,6 +62,30 @@ struct Job {
   int stable;        // 1: stop after the first step r that changes nothing
 };
 
+// One volume job of the 3D filter.  Planes: d * h rows of wpr words, bit b of
+// word j of row (y, z) = voxel (32 j + b, y, z); all in global memory.
+struct Job3 {
+  const uint8_t* in;   // dense w * h * d bytes, x fastest
+  uint8_t* out;
+  const uint8_t* C;
+  const uint8_t* D;
+  uint32_t* S;         // current set
+  uint32_t* F;         // operator input (priority source)
+  uint32_t* cand;      // candidates
+  uint32_t* M;         // points allowed to change
+  uint32_t* g0;        // input of the current HC_r / HF_r
+  uint32_t* cp;        // C cap X, or null
+  uint32_t* dp;        // D minus X, or null
+  unsigned* sync;      // 8 barrier words (zeroed before the launch)
+  int* status;
+  unsigned long long* stats;
+  int w, h, d, wpr;
+  int rmax;
+  int gang;            // CTAs of the gang
+  int cap;             // rounds allowed per level
+  int pad_;
+};
+
 // Padded plane geometry shared by both modes: rows -1..h, P words per row
 // (P = the first odd number above the words of a row; the extra words and
 // rows are zero: outside the box), one zero word before row -1, rounded up
@@ -86,6 +110,10 @@ inline size_t resident_smem_bytes(int w, int h) { return state_bytes(w, h); }
 cudaError_t upload_level_table();
 cudaError_t set_level_table_reg(const void* tab, size_t bytes);
 cudaError_t set_level_table_tiled(const void* tab, size_t bytes);
+constexpr int kMaxR3D = 12;   // largest rmax of the 3D filter
+cudaError_t upload_level_table_3d();
+int max_3d_ctas(int device);
+cudaError_t launch_3d(const Job3* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);
 cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, int grid,
                             size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
 cudaError_t launch_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);
