@@ -41,6 +41,11 @@ WORKLOAD = ("batch of 256 synthetic 512x512 binary images (discs/ellipses, holes
 # update the set; one ring read of a level update = 1 funnel shift + 1 OR.
 OPS_PER_WORD_TEST = 20
 OPS_PER_RING_EVAL = 2
+# 3D: one voxel test = 27 lane-ops to assemble the 27-bit neighbourhood plus
+# at least two dilation steps of each of the two flood fills (about 18 each),
+# counted as 100; one ring read of a word = funnel shift + AND/OR + address, 4.
+OPS_PER_VOXEL_TEST = 100
+OPS_PER_RING3_EVAL = 4
 SM_COUNT = 152
 INT32_LANES_PER_SM = 128
 
@@ -310,6 +315,136 @@ def run_serving(ctx, dev, seconds: float, rate: float = 2000.0):
     }
 
 
+def run_volume(args):
+    """The 3D filter: a batch of 16 volumes of 128^3, rmax 4, through
+    hasf_smooth3d."""
+    import numpy as np
+    import torch
+    from paper_1603_09337_gb300 import Context, _lib, build, replicas, synth
+
+    ws, rank, local = replicas.world()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    ctx = Context(local)
+    n = 16
+    jobs = synth.volume_batch(n, 128, first=rank * n)
+    Xs = [torch.from_numpy(j.X).to(dev) for j in jobs]
+    vols = [(x, j.rmax, None, None) for x, j in zip(Xs, jobs)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.smooth3d(vols)
+    ctx.status()
+    ctx.read_stats()
+    ctx.set_option(_lib.OPT_STATS, 1)
+    ctx.smooth3d(vols)
+    ctx.status()
+    stats = ctx.read_stats()
+    ctx.set_option(_lib.OPT_STATS, 0)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            ctx.smooth3d(vols)
+            ends[i].record(stream)
+        barrier()
+        wall = time.perf_counter() - wall0
+    ctx.status()
+    launches = ctx.read_stats()["launches"]
+    t_ms = replicas.max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), dev)
+    ms_per_step = t_ms / args.steps
+    value = n * args.steps * ws / (t_ms / 1e3)
+
+    e2e = None
+    if not args.no_e2e:
+        hX = [torch.from_numpy(j.X).pin_memory() for j in jobs]
+        hO = [torch.empty_like(h).pin_memory() for h in hX]
+        k = max(1, min(args.steps, 3))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k):
+            dX = [h.to(dev, non_blocking=True) for h in hX]
+            outs = ctx.smooth3d([(x, j.rmax, None, None) for x, j in zip(dX, jobs)])
+            for o, h in zip(outs, hO):
+                h.copy_(o, non_blocking=True)
+            torch.cuda.synchronize()
+        te = replicas.max_over_ranks((time.perf_counter() - t0) / k, dev)
+        e2e = {"value": n * ws / te, "unit": "volumes/s",
+               "h2d_bytes_per_step": int(sum(h.numel() for h in hX)),
+               "d2h_bytes_per_step": int(sum(h.numel() for h in hO))}
+    if rank != 0:
+        ctx.close()
+        return 0
+    peaks, peak_src = _peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = SM_COUNT * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    ops = stats["word_tests"] * OPS_PER_VOXEL_TEST + stats["ring_evals"] * OPS_PER_RING3_EVAL
+    achieved = ops / (ms_per_step / 1e3) / 1e12
+    vox = sum(x.numel() for x in Xs)
+    cpu = None
+    if not args.no_cpu and ws == 1:
+        win = jobs[0].X[:32, :32, :32].copy()
+        rate_w, cwall, cwork = cpu_oracle_rate3d(win, jobs[0].rmax)
+        scale = win.size / jobs[0].X.size
+        cpu = {"value": rate_w * scale, "unit": "volumes/s", "cores": 1, "kind": "oracle",
+               "sample": f"one 32^3 window of a volume, rmax {jobs[0].rmax}, one core, "
+                         f"{cwork:.1f} s; volumes/s scaled by the voxel ratio {scale:.5f}"}
+    line = {
+        "metric": "HASF3D volumes/s at 128^3, rmax=4", "value": value, "unit": "volumes/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 bit planes (integer only)", "data": "synthetic",
+        "config": {"workload": "batch of 16 synthetic 128^3 volumes (balls of radius 4-16, "
+                               "3% noise), rmax=4, (26,6) adjacency, one hasf_smooth3d call",
+                   "volumes_per_step": n, "mvoxel_per_s": vox * args.steps * ws / (t_ms / 1e3) / 1e6,
+                   "l2": "flushed between timed steps (256 MB write, untimed)", "wall_s": wall},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": achieved / alu_peak, "traffic": None,
+                     "peak_source": "152 SMs x 128 int32 lanes x max SM clock (recipe unit counts)",
+                     "ops_per_step": ops, "counters": stats},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _oracle3d_job(args):
+    import oracle
+    X, rmax = args
+    t = time.perf_counter()
+    oracle.hasf3d(X, rmax)
+    return time.perf_counter() - t
+
+
+def cpu_oracle_rate3d(X, rmax):
+    """Volumes/s of the 3D oracle on one host process over X."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    with mp.get_context("spawn").Pool(1) as pool:
+        t0 = time.perf_counter()
+        dt = pool.map(_oracle3d_job, [(X, rmax)])[0]
+        wall = time.perf_counter() - t0
+    return 1.0 / dt, wall, dt
+
+
 def run_hasf(args):
     import numpy as np
     import torch
@@ -514,7 +649,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hasf", choices=["hasf", "reference"])
-    ap.add_argument("--workload", default="batch512", choices=["batch512", "ragged", "large"])
+    ap.add_argument("--workload", default="batch512",
+                    choices=["batch512", "ragged", "large", "volume"])
     ap.add_argument("--ragged-n", type=int, default=1024)
     ap.add_argument("--side", type=int, default=4096)
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -526,6 +662,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "volume":
+        return run_volume(args)
     return run_hasf(args)
 
 

@@ -246,7 +246,8 @@ __device__ void snapshot3(V3& v, const Job3& jb) {
 }
 
 // CTA b works on part ctamap[b].y of job ctamap[b].x (a gang of jobs[].gang CTAs).
-__global__ void __launch_bounds__(kThreads, 1)
+// Two CTAs per SM: the sweeps wait on gang barriers, and a second CTA hides them.
+__global__ void __launch_bounds__(kThreads, 2)
 hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
   __shared__ int flag;
   const int2 m = ctamap[blockIdx.x];

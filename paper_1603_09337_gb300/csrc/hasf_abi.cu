@@ -829,10 +829,14 @@ size_t volume_bytes(const hasf_volume& v) {
   return 7 * align_up(nw * 4);
 }
 
-int volume_gang(const hasf_ctx* ctx, const hasf_volume& v) {
+// CTAs of one volume's gang: about 4 words per thread and pass, but no more
+// than the batch's share of the co-resident CTAs, so that the whole batch runs
+// in one launch (the gang barrier, not the words, bounds a sweep's time).
+int volume_gang(const hasf_ctx* ctx, const hasf_volume& v, int nvols) {
   const long long nw = (long long)v.depth * v.height * words_per_row(v.width);
-  long long g = (nw + 2047) / 2048;   // about 4 words per thread and pass
-  return (int)std::max(1LL, std::min(g, (long long)std::min(ctx->max3d, 64)));
+  long long g = (nw + 2047) / 2048;
+  const int share = std::max(1, ctx->max3d / std::max(1, nvols));
+  return (int)std::max(1LL, std::min(g, (long long)std::min({share, ctx->max3d, 64})));
 }
 
 }  // namespace
@@ -852,7 +856,7 @@ int hasf_smooth3d(hasf_ctx* ctx, const hasf_volume* vols, int n, void* stream) {
     size_t bytes = 0;
     while (first + cnt < n) {
       const hasf_volume& v = vols[first + cnt];
-      const int g = volume_gang(ctx, v);
+      const int g = volume_gang(ctx, v, n);
       const size_t b = volume_bytes(v);
       if (cnt > 0 && (ctas + g > ctx->max3d || bytes + b > ctx->budget / 2)) break;
       ctas += g;
@@ -882,7 +886,7 @@ int hasf_smooth3d(hasf_ctx* ctx, const hasf_volume* vols, int n, void* stream) {
       j.d = v.depth;
       j.wpr = words_per_row(v.width);
       j.rmax = v.rmax;
-      j.gang = volume_gang(ctx, v);
+      j.gang = volume_gang(ctx, v, n);
       const long long vox = (long long)v.width * v.height * v.depth;
       j.cap = ctx->opt.round_cap > 0 ? ctx->opt.round_cap : (int)std::min<long long>(vox + 2, INT_MAX);
       const size_t pb = align_up((size_t)v.depth * v.height * j.wpr * 4);

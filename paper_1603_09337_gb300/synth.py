@@ -209,6 +209,37 @@ def ragged_batch(n: int = 1024, first: int = 0, lo: int = 128, hi: int = 2048) -
     return jobs
 
 
+def volume(seed: int, d: int, h: int, w: int, n_balls: int, rlo: int, rhi: int,
+           noise_permille: int) -> np.ndarray:
+    """A (d, h, w) 0/1 volume: union of n_balls balls (centre uniform in the box,
+    radius uniform in [rlo, rhi], exact integer inside test), then each voxel
+    flipped with probability noise_permille / 1000."""
+    rng = SplitMix64(seed)
+    V = np.zeros((d, h, w), np.uint8)
+    for _ in range(n_balls):
+        cz, cy, cx = rng.randint(0, d - 1), rng.randint(0, h - 1), rng.randint(0, w - 1)
+        r = rng.randint(rlo, rhi)
+        z0, z1 = max(0, cz - r), min(d, cz + r + 1)
+        y0, y1 = max(0, cy - r), min(h, cy + r + 1)
+        x0, x1 = max(0, cx - r), min(w, cx + r + 1)
+        zz, yy, xx = np.ogrid[z0:z1, y0:y1, x0:x1]
+        inside = (zz - cz) ** 2 + (yy - cy) ** 2 + (xx - cx) ** 2 <= r * r
+        V[z0:z1, y0:y1, x0:x1] |= inside.astype(np.uint8)
+    flip = (rng.block(d * h * w) % np.uint64(1000)) < np.uint64(noise_permille)
+    return V ^ flip.reshape(d, h, w).astype(np.uint8)
+
+
+def volume_batch(n: int = 16, side: int = 128, first: int = 0) -> list[Job]:
+    """n volumes of side^3 voxels: balls of radius 4-16 (about 40 per 128^3,
+    scaled to volume), 3 % noise; rmax = 4.  Job.X has shape (d, h, w)."""
+    jobs = []
+    nb = max(1, (40 * side ** 3 + (1 << 20)) // (1 << 21))
+    for i in range(first, first + n):
+        seed = image_seed(5, i)
+        jobs.append(Job(volume(seed, side, side, side, nb, 4, 16, 30), 4, meta={"seed": seed}))
+    return jobs
+
+
 def small_random(seed: int, w: int, h: int, density_permille: int = 500) -> np.ndarray:
     """Independent Bernoulli pixels (for tiny brute-force checks)."""
     rng = SplitMix64(seed)
