@@ -398,32 +398,21 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
     cudaEventDestroy(ev_fork);
     return cuda_status(ej);
   };
-  if (!p.reg_order.empty()) {
-    const int per_sm = std::max(1, reg_ctas_per_sm(p.reg_smem));
-    const int grid = std::min<int>((int)p.reg_order.size(), per_sm * ctx->num_sms);
-    e = launch_reg(d_jobs, (const int*)(base + p.off_order) + p.order.size(),
-                   (int)p.reg_order.size(), grid, p.reg_smem,
-                   (unsigned*)(base + p.off_counter) + 1, lane());
-    if (e != cudaSuccess) return cuda_status(e);
-    ++ctx->launches;
-  }
-  if (!p.order.empty()) {
-    const int per_sm = std::max(1, resident_ctas_per_sm(ctx->device, p.smem));
-    const int grid = std::min<int>((int)p.order.size(), per_sm * ctx->num_sms);
-    e = launch_resident(d_jobs, (const int*)(base + p.off_order), (int)p.order.size(), grid,
-                        p.smem, (unsigned*)(base + p.off_counter), lane());
-    if (e != cudaSuccess) return cuda_status(e);
-    ++ctx->launches;
-  }
-  // Tile clusters: one launch per cluster size.
+  // Tile clusters: one launch per cluster size, the largest images first
+  // (they run longest; launched first, they do not form the tail).
   {
+    std::vector<std::pair<int, size_t>> at_of;   // (cluster size, first order slot)
     size_t at_o = p.order.size() + p.reg_order.size();
     for (const auto& kv : p.tile_groups) {
-      e = launch_tile_cluster(d_jobs, (const int*)(base + p.off_order) + at_o,
-                              (int)kv.second.size(), kv.first, lane());
+      at_of.push_back({kv.first, at_o});
+      at_o += kv.second.size();
+    }
+    for (auto it = at_of.rbegin(); it != at_of.rend(); ++it) {
+      const auto& jobs_of = p.tile_groups.at(it->first);
+      e = launch_tile_cluster(d_jobs, (const int*)(base + p.off_order) + it->second,
+                              (int)jobs_of.size(), it->first, lane());
       if (e != cudaSuccess) return cuda_status(e);
       ++ctx->launches;
-      at_o += kv.second.size();
     }
   }
   // Tiled gangs: as many whole images as fit co-resident per cooperative launch
@@ -460,6 +449,23 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
     if (e != cudaSuccess) return cuda_status(e);
     ++ctx->launches;
     at = end;
+  }
+  if (!p.reg_order.empty()) {
+    const int per_sm = std::max(1, reg_ctas_per_sm(p.reg_smem));
+    const int grid = std::min<int>((int)p.reg_order.size(), per_sm * ctx->num_sms);
+    e = launch_reg(d_jobs, (const int*)(base + p.off_order) + p.order.size(),
+                   (int)p.reg_order.size(), grid, p.reg_smem,
+                   (unsigned*)(base + p.off_counter) + 1, lane());
+    if (e != cudaSuccess) return cuda_status(e);
+    ++ctx->launches;
+  }
+  if (!p.order.empty()) {
+    const int per_sm = std::max(1, resident_ctas_per_sm(ctx->device, p.smem));
+    const int grid = std::min<int>((int)p.order.size(), per_sm * ctx->num_sms);
+    e = launch_resident(d_jobs, (const int*)(base + p.off_order), (int)p.order.size(), grid,
+                        p.smem, (unsigned*)(base + p.off_counter), lane());
+    if (e != cudaSuccess) return cuda_status(e);
+    ++ctx->launches;
   }
   return join();
 }
