@@ -529,7 +529,7 @@ def run_hasf(args):
     # The same step as plain per-image launches: one hasf_smooth per image on
     # the same stream (the alternative to the batched launch).
     per_image = None
-    if args.workload != "large":
+    if args.workload != "large" and not args.no_per_image:
         for i in range(n):
             ctx.smooth(Xs[i], jobs[i].rmax, C=Cs[i], out=outs[i], conn=jobs[i].conn)
         ctx.status()
@@ -657,6 +657,8 @@ def main():
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-per-image", action="store_true",
+                    help="skip the one-launch-per-image comparison")
     ap.add_argument("--conn", type=int, default=8, choices=[8, 4],
                     help="adjacency of the object: 8 = (8,4), 4 = (4,8)")
     args = ap.parse_args()
