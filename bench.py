@@ -59,7 +59,8 @@ def _traffic(workload: str):
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "hasf_reg_kernel_traffic.json")))
         src = b"".join(open(os.path.join(ROOT, "paper_1603_09337_gb300", "csrc", f), "rb").read()
-                       for f in ("hasf_reg.cuh", "hasf_kernels.cu", "hasf_internal.h"))
+                       for f in ("hasf_reg.cu", "hasf_reg.cuh", "hasf_device.cuh",
+                                 "hasf_internal.h"))
         if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
             return None
         return rec["dram_bytes_read"] + rec["dram_bytes_write"]
