@@ -139,6 +139,117 @@ __device__ uint32_t pack3(const uint8_t* p, int n) {
   return s;
 }
 
+// Load the 3 x 3 rows around row (y, z) at word j as 96-bit windows: bit i of
+// win[k] is voxel x = 32 j + i - 1 of row (y + k % 3 - 1, z + k / 3 - 1).
+__device__ __forceinline__ void load_window(const V3& v, const uint32_t* S, int j, int y, int z,
+                                            uint64_t (&win)[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int dy = k % 3 - 1, dz = k / 3 - 1;
+    const uint32_t p = v.ld(S, j - 1, y + dy, z + dz);
+    const uint32_t c = v.ld(S, j, y + dy, z + dz);
+    const uint32_t n = v.ld(S, j + 1, y + dy, z + dz);
+    win[k] = ((uint64_t)n << 33) | ((uint64_t)c << 1) | (uint64_t)(p >> 31);
+  }
+}
+
+// The simple voxels among the candidate bits cw of the window's centre word.
+__device__ __forceinline__ uint32_t test_bits(V3& v, const uint64_t (&win)[9], uint32_t cw) {
+  uint32_t chg = 0;
+  while (cw) {
+    const int b = __ffs(cw) - 1;
+    cw &= cw - 1u;
+    uint32_t code = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) code |= (uint32_t)((win[k] >> b) & 7u) << (3 * k);
+    ++v.n_tests;
+    if (simple3(code)) chg |= 1u << b;
+  }
+  return chg;
+}
+
+// One subfield (sx, sy, sz): every candidate voxel of it that is simple changes.
+__device__ int sweep_sub3(V3& v, const Job3& jb, bool thin, int sx, int sy, int sz) {
+  const int ny = (v.h - sy + 1) >> 1, nz = (v.d - sz + 1) >> 1;
+  const long long nsub = (long long)ny * nz * v.wpr;
+  const uint32_t xm = sx ? 0xAAAAAAAAu : 0x55555555u;
+  int changed = 0;
+  for (long long q = v.gtid; q < nsub; q += v.gthreads) {
+    const int j = (int)(q % v.wpr);
+    const long long rr = q / v.wpr;
+    const int y = sy + 2 * (int)(rr % ny), z = sz + 2 * (int)(rr / ny);
+    const long long t = ((long long)z * v.h + y) * v.wpr + j;
+    const uint32_t call = __ldcg(jb.cand + t);
+    const uint32_t cw = call & xm;
+    if (!cw) continue;
+    uint64_t win[9];
+    load_window(v, jb.S, j, y, z, win);
+    const uint32_t cur = (uint32_t)(win[4] >> 1);
+    const uint32_t chg = test_bits(v, win, cw);
+    if (chg) {
+      __stcg(jb.S + t, thin ? (cur & ~chg) : (cur | chg));
+      __stcg(jb.cand + t, call & ~chg);
+      changed = 1;
+    }
+  }
+  return changed;
+}
+
+// The two subfields (0, sy, sz) then (1, sy, sz) fused, for rows of at most 32
+// words: a row is handled by wpr consecutive lanes of one warp, which test the
+// even voxels, pass their updated words one lane to the left (an odd voxel at
+// bit 31 sees the next word's even voxel 0 as the first subfield left it),
+// then test the odd voxels.  Only the row itself changes in these two passes,
+// and a warp's lanes load everything before any of them stores.
+__device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
+  const int ny = (v.h - sy + 1) >> 1, nz = (v.d - sz + 1) >> 1;
+  const long long nrows = (long long)ny * nz;
+  const int per_warp = 32 / v.wpr;
+  const int lane = threadIdx.x & 31;
+  const int rl = lane / v.wpr, j = lane - rl * v.wpr;
+  const long long gw = v.gtid >> 5, nwarps = v.gthreads >> 5;
+  int changed = 0;
+  for (long long rb = gw * per_warp; rb < nrows; rb += nwarps * per_warp) {
+    const long long row = rb + rl;
+    const bool act = rl < per_warp && row < nrows;
+    long long t = 0;
+    uint32_t call = 0;
+    if (act) {
+      const int y = sy + 2 * (int)(row % ny), z = sz + 2 * (int)(row / ny);
+      t = ((long long)z * v.h + y) * v.wpr + j;
+      call = __ldcg(jb.cand + t);
+    }
+    if (!__any_sync(0xFFFFFFFFu, call != 0u)) continue;
+    uint64_t win[9];
+    uint32_t cur = 0, ch0 = 0;
+    if (act && call) {
+      const int y = sy + 2 * (int)(row % ny), z = sz + 2 * (int)(row / ny);
+      load_window(v, jb.S, j, y, z, win);
+      cur = (uint32_t)(win[4] >> 1);
+      ch0 = test_bits(v, win, call & 0x55555555u);
+    } else {
+      cur = act ? __ldcg(jb.S + t) : 0u;
+    }
+    const uint32_t c1 = thin ? (cur & ~ch0) : (cur | ch0);
+    uint32_t east = __shfl_down_sync(0xFFFFFFFFu, c1, 1);
+    if (j == v.wpr - 1) east = 0u;   // the next word is outside the box
+    uint32_t ch1 = 0;
+    const uint32_t cw1 = call & 0xAAAAAAAAu;
+    if (act && cw1) {
+      win[4] = ((uint64_t)east << 33) | ((uint64_t)c1 << 1) | (win[4] & 1u);
+      ch1 = test_bits(v, win, cw1);
+    }
+    __syncwarp();
+    const uint32_t chg = ch0 | ch1;
+    if (act && chg) {
+      __stcg(jb.S + t, thin ? (c1 & ~ch1) : (c1 | ch1));
+      __stcg(jb.cand + t, call & ~chg);
+      changed = 1;
+    }
+  }
+  return changed;
+}
+
 // One constrained thinning (thin) or thickening of S at radius r; the points
 // allowed to change lie in pos (if given) and not in neg (if given).
 __device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos,
@@ -190,49 +301,20 @@ __device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos
       if (round >= jb.cap) return false;
       ++v.n_rounds;
       int changed = 0;
-      for (int sub = 0; sub < 8; ++sub) {
-        const int sx = sub & 1, sy = (sub >> 1) & 1, sz = sub >> 2;
-        const int ny = (v.h - sy + 1) >> 1, nz = (v.d - sz + 1) >> 1;
-        const long long nsub = (long long)ny * nz * v.wpr;
-        const uint32_t xm = sx ? 0xAAAAAAAAu : 0x55555555u;
-        for (long long q = v.gtid; q < nsub; q += v.gthreads) {
-          const int j = (int)(q % v.wpr);
-          const long long rr = q / v.wpr;
-          const int y = sy + 2 * (int)(rr % ny), z = sz + 2 * (int)(rr / ny);
-          const long long t = ((long long)z * v.h + y) * v.wpr + j;
-          const uint32_t call = __ldcg(jb.cand + t);
-          uint32_t cw = call & xm;
-          if (!cw) continue;
-          // the 3 x 3 rows around (y, z), three words each
-          uint64_t win[9];
-#pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            const int dy = k % 3 - 1, dz = k / 3 - 1;
-            const uint32_t p = v.ld(jb.S, j - 1, y + dy, z + dz);
-            const uint32_t c = v.ld(jb.S, j, y + dy, z + dz);
-            const uint32_t n = v.ld(jb.S, j + 1, y + dy, z + dz);
-            win[k] = ((uint64_t)n << 33) | ((uint64_t)c << 1) | (uint64_t)(p >> 31);
-          }
-          const uint32_t cur = (uint32_t)(win[4] >> 1);
-          uint32_t chg = 0;
-          while (cw) {
-            const int b = __ffs(cw) - 1;
-            cw &= cw - 1u;
-            uint32_t code = 0;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) code |= (uint32_t)((win[k] >> b) & 7u) << (3 * k);
-            ++v.n_tests;
-            if (simple3(code)) chg |= 1u << b;
-          }
-          if (chg) {
-            __stcg(jb.S + t, thin ? (cur & ~chg) : (cur | chg));
-            __stcg(jb.cand + t, call & ~chg);
-            changed = 1;
-          }
+      if (v.wpr <= 32) {
+        for (int m = 0; m < 4; ++m) {   // (sy, sz) = (0,0), (1,0), (0,1), (1,1)
+          changed |= sweep_pair3(v, jb, thin, m & 1, m >> 1);
+          const int o = v.bar(m == 3 ? changed : 0);
+          if (v.failed()) return false;
+          if (m == 3) changed = o;
         }
-        const int o = v.bar(sub == 7 ? changed : 0);
-        if (v.failed()) return false;
-        if (sub == 7) changed = o;
+      } else {
+        for (int sub = 0; sub < 8; ++sub) {
+          changed |= sweep_sub3(v, jb, thin, sub & 1, (sub >> 1) & 1, sub >> 2);
+          const int o = v.bar(sub == 7 ? changed : 0);
+          if (v.failed()) return false;
+          if (sub == 7) changed = o;
+        }
       }
       if (!changed) break;
     }

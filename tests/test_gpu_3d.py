@@ -95,3 +95,12 @@ def test_bad_volumes_rejected(ctx):
         assert e.value.code == _lib.HASF_EINVAL
     with pytest.raises(ValueError):
         ctx.smooth3d([(torch.zeros((4, 4), dtype=torch.uint8, device="cuda"), 1, None, None)])
+
+
+def test_wide_rows_take_the_unfused_passes(ctx):
+    """Rows longer than 32 words (width > 1024) run the eight separate subfield
+    passes instead of the fused pairs."""
+    X = balls(9, 4, 5, 1100, 30, 1, 3, 0.05)
+    got = host(ctx.smooth3d([(dev(X), 2, None, None)])[0])
+    ctx.status()
+    np.testing.assert_array_equal(got, oracle.hasf3d(X, 2))
