@@ -50,8 +50,8 @@ SM_COUNT = 152
 INT32_LANES_PER_SM = 128
 
 
-def _traffic(workload: str):
-    """DRAM bytes per launch of the headline kernel from its last ncu capture,
+def _traffic_record(workload: str):
+    """The headline kernel's last ncu capture (DRAM and L2 bytes per launch),
     if the kernel sources are still the ones that capture measured."""
     import hashlib
     if workload != "batch512":
@@ -63,9 +63,15 @@ def _traffic(workload: str):
                                  "hasf_internal.h"))
         if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
             return None
-        return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+        return rec
     except Exception:
         return None
+
+
+def _traffic(workload: str):
+    """DRAM bytes per launch of the headline kernel (ncu), or None."""
+    rec = _traffic_record(workload)
+    return None if rec is None else rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
 def _peaks():
@@ -592,7 +598,13 @@ def run_hasf(args):
     in_bytes = sum(x.numel() for x in Xs) + sum(c.numel() for c in Cs if c is not None)
     alg_bytes = in_bytes + sum(o.numel() for o in outs)
     gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
+    rec = _traffic_record(args.workload)
     hbm = {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+           "ncu_dram_bytes_per_launch": None if rec is None else
+           rec["dram_bytes_read"] + rec["dram_bytes_write"],
+           "ncu_l2_bytes_per_launch": None if rec is None else rec.get("lts_bytes"),
+           "l2_gbs": None if rec is None or not rec.get("lts_bytes") else
+           rec["lts_bytes"] / (ms_per_step / 1e3) / 1e9,
            "peak_source": peak_src, "algorithmic_bytes_per_step": alg_bytes}
 
     cpu = None
