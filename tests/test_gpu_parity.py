@@ -293,13 +293,23 @@ def _counts(X):
 
 def test_large_image_exact_2048(ctx):
     """A 2048 x 2048 image of the large-image workload's kind (discs and
-    ellipses of semi-axes 5-200, 3 % noise), rmax 10: too large for one CTA,
-    so it runs in gang mode; equal to the oracle."""
+    ellipses of semi-axes 5-200, 3 % noise), rmax 10: sixteen tiles, one
+    thread-block cluster; equal to the oracle."""
     X = synth.shapes_image(synth.image_seed(2, 2048), 2048, 2048, 250, 5, 200, n_holes=0,
                            jitter=0, noise_permille=30)
     got = host(ctx.smooth(dev(X), 10))
     ctx.status()
     np.testing.assert_array_equal(got, oracle.hasf(X, 10))
+
+
+def test_extreme_aspect_ratios(ctx):
+    """Images at the width and height limits of the tiled paths: one row of
+    65,536 pixels (128 tiles, a tiled gang), 3 x 40,000 and 40,000 x 3."""
+    for h, w in [(1, 65536), (3, 40000), (40000, 3)]:
+        X = synth.small_random(h * 7 + w, w, h, 550)
+        got = host(ctx.smooth(dev(X), 2))
+        ctx.status()
+        np.testing.assert_array_equal(got, oracle.hasf(X, 2), err_msg=f"{h}x{w}")
 
 
 @pytest.mark.parametrize("side", [4096, 8192])
