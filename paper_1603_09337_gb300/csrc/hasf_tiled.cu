@@ -1,5 +1,9 @@
 // hasf_tiled.cu -- the tiled register kernels (images larger than one tile:
-// thread-block clusters and gangs) and their launchers.
+// thread-block clusters and gangs) and their launchers.  Both kernels are
+// built for two CTAs per SM (64 registers, 93 KB of shared memory: the
+// movable mask is read from the constraint planes in L2 instead of being kept
+// in shared memory): their sweeps wait on exchanges, and a second CTA per SM
+// fills those waits; a gang of more tiles than SMs also fits.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -10,7 +14,7 @@
 namespace hasf {
 
 // One cluster of ntx * nty CTAs per image: cluster i works on job order[i].
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ order) {
   extern __shared__ uint4 smem4[];
   uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
@@ -35,7 +39,7 @@ hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ o
 }
 
 // Gang mode with tiles: CTA b works on tile ctamap[b].y of job ctamap[b].x.
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, 2)
 hasf_tile_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) {
   extern __shared__ uint4 smem4[];
   uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);

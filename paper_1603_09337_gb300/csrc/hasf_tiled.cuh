@@ -51,7 +51,7 @@ static_assert((kHLcol + 1) % 4 == 0 && (kHRcol + 1) % 4 == 0 && kHRcand % 4 == 0
 // Both policies double-buffer the halo: exchange n fills buffer n & 1; every
 // read of a buffer happens between the barriers of exchanges n and n + 1, and
 // the next write to it comes after the barrier of exchange n + 1.
-constexpr int kTileSmemWords = kTileF + 2 * kRegPlane + kRegXchg + 2 * kHaloWords + 8;
+constexpr int kTileSmemWords = kTileF + kRegPlane + kRegXchg + 2 * kHaloWords + 8;
 
 __host__ __device__ inline int tiles_x(int w) { return (words_per_row(w) + kTW - 1) / kTW; }
 __host__ __device__ inline int tiles_y(int h) { return (h + kTH - 1) / kTH; }
@@ -110,7 +110,6 @@ template <class X>
 struct TileCtx {
   X x;
   Ctx<SmemMode> g;   // image geometry and counters; g.F = F plane at (row 0, word 0)
-  uint32_t* M;       // 512 x kRegPitch
   uint32_t* cand;    // 512 x kRegPitch
   uint32_t* xtop;    // [warp][16] first row of each warp of this tile
   uint32_t* xbot;    // [warp][16] last row of each warp
@@ -357,7 +356,6 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r,
     }
     g.F[R * kFP + k.j] = S[q];
     k.x.f_publish(R, k.j, S[q]);
-    k.M[R * kRegPitch + k.j] = m;
     k.cand[R * kRegPitch + k.j] = 0u;
   }
   if (k.half == 0) k.xtop[k.warp * kTW + k.j] = S[0];
@@ -401,8 +399,14 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r,
         const int q = g4 + u;
         pend[u] = 0u;
         if ((pendrows >> q) & 1u) {
-          const int a = (k.s0 + q) * kRegPitch + k.j;
-          pend[u] = k.M[a] & (thin ? S[q] : ~S[q]) & ~k.cand[a];
+          // the movable mask, read again from the constraint planes (L2)
+          // rather than kept in shared memory
+          const int R = k.s0 + q;
+          const int t = (k.y0 + R) * g.wpr + k.x0w + k.j;
+          uint32_t m = g.rowmask(k.x0w + k.j);
+          if (pos) m &= __ldcg(pos + t);
+          if (neg) m &= ~__ldcg(neg + t);
+          pend[u] = m & (thin ? S[q] : ~S[q]) & ~k.cand[R * kRegPitch + k.j];
           if (!pend[u]) pendrows &= ~(1u << q);
         }
         acc[u] = thin ? 0xFFFFFFFFu : 0u;
@@ -554,8 +558,7 @@ __device__ __forceinline__ void tile_init(TileCtx<X>& k, const Job& jb, uint32_t
   g.F = smem + 1 + kTPad * kFP + 1;   // row 0, word 0 (word -1 is one to the left)
   g.cap = jb.cap;
   g.n_tests = g.n_ring = g.n_passes = g.n_levels = g.n_rounds = 0;
-  k.M = smem + kTileF;
-  k.cand = k.M + kRegPlane;
+  k.cand = smem + kTileF;
   k.xtop = k.cand + kRegPlane;
   k.xbot = k.xtop + (kThreads / 32) * kTW;
   k.halo2 = k.xbot + (kThreads / 32) * kTW;
