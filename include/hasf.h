@@ -33,9 +33,10 @@
  *
  * Errors.  Every entry point returns a hasf_status and never aborts the
  * process.  Argument errors are reported before any device work is issued.
- * Device-side failures (an iteration cap or a wait deadline) are reported as
- * HASF_ETIMEOUT by the next synchronising call (hasf_status_of / hasf_poll /
- * the host-buffer entry points); a CUDA runtime error is HASF_ECUDA.
+ * Device-side outcomes (an iteration cap or a wait deadline: HASF_ETIMEOUT;
+ * a run to stability that reached its cap: HASF_EUNSTABLE) are reported by
+ * the next synchronising call (hasf_status_of / hasf_poll / the host-buffer
+ * entry points); a CUDA runtime error is HASF_ECUDA.
  *
  * Streams.  `stream` arguments are cudaStream_t values passed as void*
  * (NULL = the legacy default stream).  Calls on one context must be issued to
