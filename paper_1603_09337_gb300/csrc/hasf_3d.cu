@@ -19,7 +19,11 @@
 // Layout: each plane is d * h rows of ceil(w / 32) words (bit b of word j of
 // row (y, z) = voxel (32 j + b, y, z)), in global memory (L2).  A volume is
 // processed by a gang of co-resident CTAs meeting at the bounded gang barrier
-// after every phase.
+// after every phase.  Plain (L1-cacheable) loads and stores: within a phase no
+// word is written that another thread reads, and the barrier between phases
+// (fence and counter release, counter poll and fence acquire, then the CTA
+// barrier) orders every write before every later read, as a grid-wide sync
+// does; one thread only ever reads back its own candidate words.
 #include <cstdint>
 #include <algorithm>
 #include <mutex>
@@ -29,6 +33,8 @@
 #include "hasf_device.cuh"
 
 namespace hasf {
+
+__device__ __forceinline__ void st_plain(uint32_t* p, uint32_t v) { *p = v; }
 
 constexpr int kMaxR3 = kMaxR3D;
 constexpr int kMaxOff3 = 7300;   // lattice vectors with 0 < |v|^2 <= 144
@@ -122,7 +128,7 @@ struct V3 {
   }
   __device__ __forceinline__ uint32_t ld(const uint32_t* P, int j, int y, int z) const {
     if (j < 0 || j >= wpr || y < 0 || y >= h || z < 0 || z >= d) return 0u;
-    return __ldcg(P + ((long long)z * h + y) * wpr + j);
+    return P[((long long)z * h + y) * wpr + j];
   }
 };
 
@@ -179,7 +185,7 @@ __device__ int sweep_sub3(V3& v, const Job3& jb, bool thin, int sx, int sy, int 
     const long long rr = q / v.wpr;
     const int y = sy + 2 * (int)(rr % ny), z = sz + 2 * (int)(rr / ny);
     const long long t = ((long long)z * v.h + y) * v.wpr + j;
-    const uint32_t call = __ldcg(jb.cand + t);
+    const uint32_t call = (*(jb.cand + t));
     const uint32_t cw = call & xm;
     if (!cw) continue;
     uint64_t win[9];
@@ -187,8 +193,8 @@ __device__ int sweep_sub3(V3& v, const Job3& jb, bool thin, int sx, int sy, int 
     const uint32_t cur = (uint32_t)(win[4] >> 1);
     const uint32_t chg = test_bits(v, win, cw);
     if (chg) {
-      __stcg(jb.S + t, thin ? (cur & ~chg) : (cur | chg));
-      __stcg(jb.cand + t, call & ~chg);
+      st_plain(jb.S + t, thin ? (cur & ~chg) : (cur | chg));
+      st_plain(jb.cand + t, call & ~chg);
       changed = 1;
     }
   }
@@ -217,7 +223,7 @@ __device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
     if (act) {
       const int y = sy + 2 * (int)(row % ny), z = sz + 2 * (int)(row / ny);
       t = ((long long)z * v.h + y) * v.wpr + j;
-      call = __ldcg(jb.cand + t);
+      call = (*(jb.cand + t));
     }
     if (!__any_sync(0xFFFFFFFFu, call != 0u)) continue;
     uint64_t win[9];
@@ -228,7 +234,7 @@ __device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
       cur = (uint32_t)(win[4] >> 1);
       ch0 = test_bits(v, win, call & 0x55555555u);
     } else {
-      cur = act ? __ldcg(jb.S + t) : 0u;
+      cur = act ? (*(jb.S + t)) : 0u;
     }
     const uint32_t c1 = thin ? (cur & ~ch0) : (cur | ch0);
     uint32_t east = __shfl_down_sync(0xFFFFFFFFu, c1, 1);
@@ -242,8 +248,8 @@ __device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
     __syncwarp();
     const uint32_t chg = ch0 | ch1;
     if (act && chg) {
-      __stcg(jb.S + t, thin ? (c1 & ~ch1) : (c1 | ch1));
-      __stcg(jb.cand + t, call & ~chg);
+      st_plain(jb.S + t, thin ? (c1 & ~ch1) : (c1 | ch1));
+      st_plain(jb.cand + t, call & ~chg);
       changed = 1;
     }
   }
@@ -255,13 +261,13 @@ __device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
 __device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos,
                     const uint32_t* neg) {
   for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
-    const uint32_t s = __ldcg(jb.S + t);
-    __stcg(jb.F + t, s);
+    const uint32_t s = (*(jb.S + t));
+    st_plain(jb.F + t, s);
     uint32_t m = v.rowmask((int)(t % v.wpr));
-    if (pos) m &= __ldcg(pos + t);
-    if (neg) m &= ~__ldcg(neg + t);
-    __stcg(jb.M + t, m);
-    __stcg(jb.cand + t, 0u);
+    if (pos) m &= (*(pos + t));
+    if (neg) m &= ~(*(neg + t));
+    st_plain(jb.M + t, m);
+    st_plain(jb.cand + t, 0u);
   }
   v.bar(0);
   if (v.failed()) return false;
@@ -271,8 +277,8 @@ __device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos
     int any = 0;
     const int o0 = c_lv3.start[li], o1 = c_lv3.start[li + 1];
     for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
-      const uint32_t s = __ldcg(jb.S + t), c = __ldcg(jb.cand + t);
-      const uint32_t pend = __ldcg(jb.M + t) & (thin ? s : ~s) & ~c;
+      const uint32_t s = (*(jb.S + t)), c = (*(jb.cand + t));
+      const uint32_t pend = (*(jb.M + t)) & (thin ? s : ~s) & ~c;
       if (!pend) continue;
       int j, y, z;
       word_pos(v, t, j, y, z);
@@ -288,7 +294,7 @@ __device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos
       }
       const uint32_t add = pend & (thin ? ~acc : acc);
       if (add) {
-        __stcg(jb.cand + t, c | add);
+        st_plain(jb.cand + t, c | add);
         any = 1;
       }
     }
@@ -323,7 +329,7 @@ __device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos
 }
 
 __device__ void snapshot3(V3& v, const Job3& jb) {
-  for (long long t = v.gtid; t < v.nw; t += v.gthreads) __stcg(jb.g0 + t, __ldcg(jb.S + t));
+  for (long long t = v.gtid; t < v.nw; t += v.gthreads) st_plain(jb.g0 + t, (*(jb.S + t)));
   v.bar(0);
 }
 
@@ -354,9 +360,9 @@ hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
     const long long off = ((long long)z * jb.h + y) * jb.w + 32LL * j;
     const int n = min(32, jb.w - 32 * j);
     const uint32_t x = pack3(jb.in + off, n);
-    __stcg(jb.S + t, x);
-    if (jb.cp) __stcg(jb.cp + t, jb.C ? (pack3(jb.C + off, n) & x) : 0u);
-    if (jb.dp) __stcg(jb.dp + t, jb.D ? (pack3(jb.D + off, n) & ~x) : 0u);
+    st_plain(jb.S + t, x);
+    if (jb.cp) st_plain(jb.cp + t, jb.C ? (pack3(jb.C + off, n) & x) : 0u);
+    if (jb.dp) st_plain(jb.dp + t, jb.D ? (pack3(jb.D + off, n) & ~x) : 0u);
   }
   v.bar(0);
   bool ok = !v.failed();
@@ -371,7 +377,7 @@ hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
     for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
       int j, y, z;
       word_pos(v, t, j, y, z);
-      const uint32_t s = __ldcg(jb.S + t);
+      const uint32_t s = (*(jb.S + t));
       uint8_t* o = jb.out + ((long long)z * jb.h + y) * jb.w + 32LL * j;
       const int n = min(32, jb.w - 32 * j);
       for (int b = 0; b < n; ++b) o[b] = (uint8_t)((s >> b) & 1u);
