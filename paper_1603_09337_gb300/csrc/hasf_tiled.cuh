@@ -399,13 +399,14 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r,
         const int q = g4 + u;
         pend[u] = 0u;
         if ((pendrows >> q) & 1u) {
-          // the movable mask, read again from the constraint planes (L2)
-          // rather than kept in shared memory
+          // the movable mask, read again from the constraint planes rather
+          // than kept in shared memory (this tile's words of them are written
+          // by this CTA only, so cached loads see its own writes)
           const int R = k.s0 + q;
           const int t = (k.y0 + R) * g.wpr + k.x0w + k.j;
           uint32_t m = g.rowmask(k.x0w + k.j);
-          if (pos) m &= __ldcg(pos + t);
-          if (neg) m &= ~__ldcg(neg + t);
+          if (pos) m &= pos[t];
+          if (neg) m &= ~neg[t];
           pend[u] = m & (thin ? S[q] : ~S[q]) & ~k.cand[R * kRegPitch + k.j];
           if (!pend[u]) pendrows &= ~(1u << q);
         }
