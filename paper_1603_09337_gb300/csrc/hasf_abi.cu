@@ -428,7 +428,7 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
         if (end > at && (int)(end - at) + gsz > ctx->tile_gang_max) break;
         end += gsz;
       }
-      e = launch_tile_gang(d_jobs, d_tmap + at, (int)(end - at), ls);
+      e = launch_tile_gang(d_jobs, d_tmap + at, (int)(end - at), groups == 1, ls);
       if (e != cudaSuccess) return cuda_status(e);
       ++ctx->launches;
       at = end;

@@ -129,7 +129,8 @@ int tile_clusters_possible(int csize);
 cudaError_t launch_tile_cluster(const Job* d_jobs, const int* d_order, int njobs, int csize,
                                 cudaStream_t s);
 int max_tile_gang_ctas(int device);
-cudaError_t launch_tile_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);
+cudaError_t launch_tile_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, bool alone,
+                             cudaStream_t s);
 constexpr int kTileMaxR = 31;   // the tiled kernels take rmax <= 31
 int max_gang_ctas(int device);
 size_t max_resident_smem(int device);

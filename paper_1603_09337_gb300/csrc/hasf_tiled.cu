@@ -39,7 +39,10 @@ hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ o
 }
 
 // Gang mode with tiles: CTA b works on tile ctamap[b].y of job ctamap[b].x.
-__global__ void __launch_bounds__(kThreads, 2)
+// MINB = 2 is the default; a launch that has the GPU to itself and no more
+// tiles than SMs uses MINB = 1 (one CTA per SM with twice the registers).
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 hasf_tile_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) {
   extern __shared__ uint4 smem4[];
   uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
@@ -119,21 +122,25 @@ cudaError_t launch_tile_cluster(const Job* d_jobs, const int* d_order, int njobs
 int max_tile_gang_ctas(int device) {
   int per_sm = 0, sms = 0;
   const size_t smem = tile_smem_bytes();
-  cudaFuncSetAttribute(hasf_tile_gang_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(hasf_tile_gang_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hasf_tile_gang_kernel, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hasf_tile_gang_kernel<2>, kThreads, smem);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   return per_sm * sms;
 }
 
-cudaError_t launch_tile_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s) {
+cudaError_t launch_tile_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, bool alone,
+                             cudaStream_t s) {
   const size_t smem = tile_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(hasf_tile_gang_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void* fn = (alone && nctas <= sms) ? (const void*)hasf_tile_gang_kernel<1>
+                                           : (const void*)hasf_tile_gang_kernel<2>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   void* args[] = {(void*)&d_jobs, (void*)&d_ctamap};
-  return cudaLaunchCooperativeKernel((const void*)hasf_tile_gang_kernel, dim3(nctas),
-                                     dim3(kThreads), args, smem, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(nctas), dim3(kThreads), args, smem, s);
 }
 
 }  // namespace hasf
