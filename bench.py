@@ -74,6 +74,24 @@ def _traffic(workload: str):
     return None if rec is None else rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the CPU legs."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -194,7 +212,7 @@ def run_reference(args):
         "impl": "reference",
         "config": {"workload": WORKLOAD + f"; reference arm: the CPU oracle, {per_step} images "
                    "per step (one per host core)", "images_per_step": per_step},
-        "cpu_baseline": {"value": value, "unit": "images/s", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "images/s", "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
                          "sample": f"{per_step * args.steps} images of the workload, "
                                    f"{per_step} per step, one oracle process per core"},
         "e2e": {"value": value, "unit": "images/s", "h2d_bytes_per_step": 0,
@@ -407,7 +425,7 @@ def run_volume(args):
         win = jobs[0].X[:32, :32, :32].copy()
         rate_w, cwall, cwork = cpu_oracle_rate3d(win, jobs[0].rmax)
         scale = win.size / jobs[0].X.size
-        cpu = {"value": rate_w * scale, "unit": "volumes/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": rate_w * scale, "unit": "volumes/s", "cores": 1, "kind": "oracle", "cpu": _cpu_model(),
                "sample": f"one 32^3 window of a volume, rmax {jobs[0].rmax}, one core, "
                          f"{cwork:.1f} s; volumes/s scaled by the voxel ratio {scale:.5f}"}
     line = {
@@ -617,7 +635,7 @@ def run_hasf(args):
         for j in sample:
             j.conn = args.conn
         rate, cwall, cwork = cpu_oracle_rate(sample, cores)
-        cpu = {"value": rate, "unit": "images/s", "cores": cores, "kind": "oracle",
+        cpu = {"value": rate, "unit": "images/s", "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
                "sample": f"{len(sample)} images of the workload (other seeds), one oracle "
                          f"process per core, {cwork:.1f} s of CPU work in {cwall:.1f} s",
                "sequential_method_ops_per_image": cpu_oracle_rate.seq_ops_per_image}
@@ -629,7 +647,7 @@ def run_hasf(args):
         win = jobs[0].X[:1024, :1024].copy()
         rate_w, cwall, cwork = cpu_oracle_rate([synth.Job(win, jobs[0].rmax, conn=args.conn)], 1)
         scale = win.size / jobs[0].X.size
-        cpu = {"value": rate_w * scale, "unit": "images/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": rate_w * scale, "unit": "images/s", "cores": 1, "kind": "oracle", "cpu": _cpu_model(),
                "sample": f"one 1024x1024 window of the image, rmax {jobs[0].rmax}, one core, "
                          f"{cwork:.1f} s; images/s scaled by the pixel ratio {scale:.4f}"}
 
