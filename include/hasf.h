@@ -125,8 +125,13 @@ int hasf_smooth_batch(hasf_ctx *ctx, const hasf_image *imgs, int n, void *stream
 int hasf_status_of(hasf_ctx *ctx, void *stream);
 
 /* Host-buffer form: every pointer in `imgs` is a HOST pointer (ordinary or
- * pinned memory).  The library stages the images through pinned buffers,
- * smooths them in batches and copies the results back before returning.
+ * pinned memory).  Images whose buffers are all page-locked and mapped into
+ * the device's address space (cudaHostAlloc, or cudaHostRegister with the
+ * mapped flag) are gathered into device buffers by one launch of the
+ * library's copy kernel (reading across the host link) and scattered back by
+ * another; the others are staged through the context's pinned buffer with one
+ * copy per buffer.  Synchronous: the results are in the callers' buffers on
+ * return.
  * Errors as hasf_smooth_batch, plus HASF_ETIMEOUT. */
 int hasf_smooth_host(hasf_ctx *ctx, const hasf_image *imgs, int n);
 
@@ -169,7 +174,11 @@ int hasf_drain(hasf_ctx *ctx);
  *                        run on the tiled register kernel -- 1 (default): as
  *                        thread-block clusters when they have at most 16 tiles
  *                        of 512 x 512, else as a gang; 2: always as a gang;
- *                        0: never (generic kernels).
+ *                        0: never (generic kernels);
+ *   HASF_OPT_HOST_MAPPED (0/1): hasf_smooth_host moves page-locked,
+ *                        device-mapped caller buffers with one launch of the
+ *                        library's copy kernel per direction (1, default)
+ *                        instead of one copy call per buffer (0).
  * Errors: HASF_EINVAL for an unknown option or value. */
 enum {
     HASF_OPT_FORCE_GANG = 1,
@@ -179,7 +188,8 @@ enum {
     HASF_OPT_SERVE_BATCH = 5,
     HASF_OPT_STATS = 6,
     HASF_OPT_GENERIC_ONLY = 7,
-    HASF_OPT_TILES = 8
+    HASF_OPT_TILES = 8,
+    HASF_OPT_HOST_MAPPED = 9
 };
 int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
 

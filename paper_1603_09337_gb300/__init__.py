@@ -217,19 +217,24 @@ class Context:
 
     # -- host-buffer entry point -----------------------------------------------
     def smooth_host(self, jobs):
-        """jobs: list of (X numpy (h, w) uint8, rmax, C or None, D or None, conn, out numpy)."""
+        """jobs: list of (X numpy (h, w) uint8, rmax, C or None, D or None, conn, out
+        numpy).  The arrays of one job may be row-strided views (pixels adjacent
+        in a row) sharing one row stride, the pitch."""
         arr = (_lib.HasfImage * max(1, len(jobs)))()
         keep = []
         for i, (X, rmax, C, D, conn, out) in enumerate(jobs):
             h, w = X.shape
+            pitch = X.strides[0]
             for a in (X, C, D, out):
                 if a is not None:
-                    assert a.flags["C_CONTIGUOUS"] and a.dtype.itemsize == 1 and a.shape == (h, w)
+                    if (a.dtype.itemsize != 1 or a.shape != (h, w) or a.strides[1] != 1
+                            or a.strides[0] != pitch):
+                        raise ValueError("host images: (h, w) uint8, one row stride per job")
                     keep.append(a)
             arr[i] = _lib.HasfImage(X.ctypes.data, out.ctypes.data,
                                     C.ctypes.data if C is not None else None,
                                     D.ctypes.data if D is not None else None,
-                                    w, h, w, rmax, conn, 0)
+                                    w, h, pitch, rmax, conn, 0)
         check(self.lib.hasf_smooth_host(self.h, arr, len(jobs)), "hasf_smooth_host")
 
     # -- serving ------------------------------------------------------------------

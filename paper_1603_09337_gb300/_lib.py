@@ -22,6 +22,7 @@ OPT_FORCE_GANG, OPT_GANG_CTAS, OPT_ROUND_CAP, OPT_SERVE_STREAMS, OPT_SERVE_BATCH
 OPT_STATS = 6
 OPT_GENERIC_ONLY = 7
 OPT_TILES = 8
+OPT_HOST_MAPPED = 9
 STAT_NAMES = ("word_tests", "ring_evals", "passes", "levels", "rounds", "launches")
 
 OP_THIN, OP_THICK, OP_HC, OP_HF = 1, 2, 3, 4

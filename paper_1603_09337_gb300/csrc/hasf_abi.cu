@@ -84,6 +84,7 @@ struct Options {
   int serve_batch = 512;
   int stats = 0;
   int generic_only = 0;
+  int host_mapped = 1;  // hasf_smooth_host: mapped pinned buffers used in place
 };
 
 struct Batch {  // one server launch in flight
@@ -799,6 +800,10 @@ int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
       ctx->opt.no_tiles = value == 0;
       ctx->opt.tile_force = (int)value == 2 ? 2 : 0;
       return HASF_OK;
+    case HASF_OPT_HOST_MAPPED:
+      if (value != 0 && value != 1) return HASF_EINVAL;
+      ctx->opt.host_mapped = (int)value;
+      return HASF_OK;
     default:
       return HASF_EINVAL;
   }
@@ -954,6 +959,121 @@ bool is_pinned(const void* p) {
   }
   return a.type == cudaMemoryTypeHost;
 }
+
+// The device address of a page-locked host buffer mapped into the device's
+// address space, or null.
+void* mapped_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// The image with every buffer replaced by its device mapping, if they all
+// have one.
+bool mapped_image(const hasf_image& im, hasf_image& out) {
+  out = im;
+  void* in = mapped_ptr(im.in);
+  void* o = mapped_ptr(im.out);
+  if (!in || !o) return false;
+  out.in = (const uint8_t*)in;
+  out.out = (uint8_t*)o;
+  if (im.C) {
+    void* c = mapped_ptr(im.C);
+    if (!c) return false;
+    out.C = (const uint8_t*)c;
+  }
+  if (im.D) {
+    void* d = mapped_ptr(im.D);
+    if (!d) return false;
+    out.D = (const uint8_t*)d;
+  }
+  return true;
+}
+
+int smooth_host_staged(hasf_ctx* ctx, const hasf_image* imgs, int n);
+
+// Images whose host buffers are all mapped (maps: the same images with the
+// device addresses of those buffers): per chunk, one launch of the library's
+// copy kernel gathers every input into device buffers, one batched smoothing
+// runs, one copy launch scatters the results back to the callers' buffers.
+int smooth_host_mapped(hasf_ctx* ctx, const hasf_image* maps, int n) {
+  cudaStream_t s = ctx->host_stream;
+  auto dpitch = [](const hasf_image& im) { return ((size_t)im.width + 15) & ~(size_t)15; };
+  auto slots = [](const hasf_image& im) { return 2 + (im.C ? 1 : 0) + (im.D ? 1 : 0); };
+  auto img_bytes = [&](const hasf_image& im) {
+    return align_up(dpitch(im) * im.height) * slots(im);
+  };
+  const size_t io_cap = std::max<size_t>(ctx->budget / 4, 64ull << 20);
+  int first = 0;
+  while (first < n) {
+    int cnt = 0;
+    size_t io = 0;
+    while (first + cnt < n && (cnt == 0 || io + img_bytes(maps[first + cnt]) <= io_cap)) {
+      io += img_bytes(maps[first + cnt]);
+      ++cnt;
+    }
+    const size_t desc_at = align_up(io);
+    const size_t need = desc_at + align_up(sizeof(Copy2D) * 4 * (size_t)cnt);
+    if (ctx->io_bytes < need) {
+      cudaStreamSynchronize(s);
+      if (ctx->io) cudaFree(ctx->io);
+      ctx->io = nullptr;
+      ctx->io_bytes = 0;
+      if (cudaMalloc(&ctx->io, need) != cudaSuccess) {
+        cudaGetLastError();
+        return HASF_ENOMEM;
+      }
+      ctx->io_bytes = need;
+    }
+    char* dev = (char*)ctx->io;
+    std::vector<hasf_image> dimgs(cnt);
+    std::vector<Copy2D> copies;   // the gathers, then the scatters
+    std::vector<Copy2D> back;
+    size_t at = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const hasf_image& m = maps[first + i];
+      const size_t dp = dpitch(m), sb = align_up(dp * m.height);
+      hasf_image& di = dimgs[i];
+      di = m;
+      di.pitch = (int32_t)dp;
+      char* base = dev + at;
+      di.in = (const uint8_t*)base;
+      di.out = (uint8_t*)(base + sb);
+      size_t k = 2;
+      copies.push_back({m.in, (uint8_t*)base, m.width, m.height, m.pitch, (int)dp});
+      if (m.C) {
+        di.C = (const uint8_t*)(base + sb * k++);
+        copies.push_back({m.C, (uint8_t*)di.C, m.width, m.height, m.pitch, (int)dp});
+      }
+      if (m.D) {
+        di.D = (const uint8_t*)(base + sb * k++);
+        copies.push_back({m.D, (uint8_t*)di.D, m.width, m.height, m.pitch, (int)dp});
+      }
+      back.push_back({di.out, m.out, m.width, m.height, (int)dp, m.pitch});
+      at += img_bytes(m);
+    }
+    const int nin = (int)copies.size();
+    copies.insert(copies.end(), back.begin(), back.end());
+    Copy2D* d_copies = (Copy2D*)(dev + desc_at);
+    cudaError_t e = cudaMemcpyAsync(d_copies, copies.data(), sizeof(Copy2D) * copies.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_copy2d(d_copies, nin, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    ctx->launches += (nin + 65534) / 65535;
+    int rc = run_images(ctx, dimgs.data(), cnt, OP_HASF, s);
+    if (rc) return rc;
+    e = launch_copy2d(d_copies + nin, cnt, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    ctx->launches += (cnt + 65534) / 65535;
+    rc = hasf_status_of(ctx, s);   // also: the chunk's buffers are free again
+    if (rc) return rc;
+    first += cnt;
+  }
+  return HASF_OK;
+}
 }  // namespace
 
 int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
@@ -965,6 +1085,24 @@ int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
   if (n == 0) return HASF_OK;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_status(e);
+  // Mapped page-locked images move through the copy kernel; the rest are
+  // staged through the context's pinned buffer with one copy per buffer.
+  std::vector<hasf_image> mapped, staged;
+  for (int i = 0; i < n; ++i) {
+    hasf_image m;
+    if (ctx->opt.host_mapped && mapped_image(imgs[i], m)) mapped.push_back(m);
+    else staged.push_back(imgs[i]);
+  }
+  if (!mapped.empty()) {
+    int rc = smooth_host_mapped(ctx, mapped.data(), (int)mapped.size());
+    if (rc) return rc;
+  }
+  return staged.empty() ? HASF_OK : smooth_host_staged(ctx, staged.data(), (int)staged.size());
+}
+
+namespace {
+int smooth_host_staged(hasf_ctx* ctx, const hasf_image* imgs, int n) {
+  cudaError_t e = cudaSuccess;
   cudaStream_t s = ctx->host_stream;
   // Device layout of one image: in, out, [C], [D], each w*h bytes, pitch w.
   auto img_bytes = [](const hasf_image& im) {
@@ -1070,6 +1208,7 @@ int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
   }
   return HASF_OK;
 }
+}  // namespace
 
 int hasf_submit(hasf_ctx* ctx, const hasf_image* img, uint64_t* ticket) {
   if (!ctx || !img || !ticket) return HASF_EINVAL;

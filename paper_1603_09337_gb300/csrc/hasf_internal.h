@@ -136,6 +136,13 @@ int max_gang_ctas(int device);
 size_t max_resident_smem(int device);
 int resident_ctas_per_sm(int device, size_t smem_bytes);
 cudaError_t launch_simple_table(int conn, uint8_t* d_out256, cudaStream_t s);
+// One 2D byte copy: h rows of w bytes, row pitches in bytes.
+struct Copy2D {
+  const uint8_t* src;
+  uint8_t* dst;
+  int w, h, spitch, dpitch;
+};
+cudaError_t launch_copy2d(const Copy2D* d_copies, int n, cudaStream_t s);
 cudaError_t launch_levels(const uint8_t* feat, int w, int h, int pitch, int mode, int r,
                           uint32_t* d_plane_f, uint32_t* d_plane_a, int32_t* d, cudaStream_t s);
 cudaError_t launch_edt(const uint8_t* feat, int w, int h, int pitch, int outside, int32_t* g,

@@ -218,6 +218,41 @@ cudaError_t launch_simple_table(int conn, uint8_t* d_out256, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// A batch of 2D byte copies in one launch (host buffers mapped into the
+// device's address space to or from device buffers): blockIdx.y is the copy,
+// the blocks along x stride over its 16-byte chunks (or bytes, when a row or
+// a pointer is not 16-byte aligned).
+__global__ void __launch_bounds__(256) copy2d_kernel(const Copy2D* __restrict__ copies) {
+  const Copy2D c = copies[blockIdx.y];
+  const bool vec = ((reinterpret_cast<uintptr_t>(c.src) | reinterpret_cast<uintptr_t>(c.dst) |
+                     (uintptr_t)c.spitch | (uintptr_t)c.dpitch | (uintptr_t)c.w) & 15u) == 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long first = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    const int cpr = c.w >> 4;
+    const long long total = (long long)c.h * cpr;
+    for (long long i = first; i < total; i += stride) {
+      const int y = (int)(i / cpr), k = (int)(i - (long long)y * cpr);
+      reinterpret_cast<uint4*>(c.dst + (size_t)y * c.dpitch)[k] =
+          reinterpret_cast<const uint4*>(c.src + (size_t)y * c.spitch)[k];
+    }
+  } else {
+    const long long total = (long long)c.h * c.w;
+    for (long long i = first; i < total; i += stride) {
+      const int y = (int)(i / c.w), x = (int)(i - (long long)y * c.w);
+      c.dst[(size_t)y * c.dpitch + x] = c.src[(size_t)y * c.spitch + x];
+    }
+  }
+}
+
+cudaError_t launch_copy2d(const Copy2D* d_copies, int n, cudaStream_t s) {
+  for (int at = 0; at < n; at += 65535) {
+    const int m = n - at < 65535 ? n - at : 65535;
+    copy2d_kernel<<<dim3(16, m), 256, 0, s>>>(d_copies + at);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_levels(const uint8_t* feat, int w, int h, int pitch, int mode, int r,
                           uint32_t* d_plane_f, uint32_t* d_plane_a, int32_t* d, cudaStream_t s) {
   const int pw = plane_words(w, h);

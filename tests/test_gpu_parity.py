@@ -241,6 +241,37 @@ def test_host_buffers(ctx):
         np.testing.assert_array_equal(o, oracle.hasf(X, r, C=C, conn=cn))
 
 
+def test_host_buffers_pinned_mapped_and_staged(ctx):
+    """Pinned host buffers, some with padded rows, one job pageable: moved by
+    the library's copy kernel over the mapping, or by one copy per buffer;
+    the results equal the oracle and the row padding is left untouched."""
+    import torch
+    jobs = _mixed_jobs()[:6]
+    for mapped in (1, 0):
+        ctx.set_option(_lib.OPT_HOST_MAPPED, mapped)
+        specs, pads = [], []
+        for k, (X, r, C, cn) in enumerate(jobs):
+            h, w = X.shape
+            pitch = w + 16 * (k % 3)
+            def buf(fill):
+                b = torch.full((h, pitch), fill, dtype=torch.uint8)
+                return (b.pin_memory() if k != 5 else b).numpy()
+            bx, bo = buf(0), buf(7)
+            bx[:, :w] = X
+            bc = None
+            if C is not None:
+                bc = buf(0)
+                bc[:, :w] = C
+            specs.append((bx[:, :w], r, None if bc is None else bc[:, :w], None, cn, bo[:, :w]))
+            pads.append(bo)
+        ctx.smooth_host(specs)
+        for (X, r, C, cn), bo in zip(jobs, pads):
+            w = X.shape[1]
+            np.testing.assert_array_equal(bo[:, :w], oracle.hasf(X, r, C=C, conn=cn))
+            assert (bo[:, w:] == 7).all()
+    ctx.set_option(_lib.OPT_HOST_MAPPED, 1)
+
+
 def test_invalid_arguments(ctx):
     import ctypes
     X = dev(np.zeros((8, 8), np.uint8))
