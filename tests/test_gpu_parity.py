@@ -270,6 +270,14 @@ def test_host_buffers_pinned_mapped_and_staged(ctx):
             np.testing.assert_array_equal(bo[:, :w], oracle.hasf(X, r, C=C, conn=cn))
             assert (bo[:, w:] == 7).all()
     ctx.set_option(_lib.OPT_HOST_MAPPED, 1)
+    # a batch large enough to run as two halves on two streams
+    xs = [case_image(300 + i, 40 + i, 70 - i) for i in range(40)]
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    hx = [pin(x) for x in xs]
+    ho = [pin(np.zeros_like(x)) for x in xs]
+    ctx.smooth_host([(x, 1 + i % 3, None, None, 8, o) for i, (x, o) in enumerate(zip(hx, ho))])
+    for i, (x, o) in enumerate(zip(xs, ho)):
+        np.testing.assert_array_equal(o, oracle.hasf(x, 1 + i % 3), err_msg=f"image {i}")
 
 
 def test_invalid_arguments(ctx):
