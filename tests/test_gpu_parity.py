@@ -270,7 +270,7 @@ def test_host_buffers_pinned_mapped_and_staged(ctx):
             np.testing.assert_array_equal(bo[:, :w], oracle.hasf(X, r, C=C, conn=cn))
             assert (bo[:, w:] == 7).all()
     ctx.set_option(_lib.OPT_HOST_MAPPED, 1)
-    # a batch large enough to run as two halves on two streams
+    # forty pinned images in one call
     xs = [case_image(300 + i, 40 + i, 70 - i) for i in range(40)]
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     hx = [pin(x) for x in xs]
