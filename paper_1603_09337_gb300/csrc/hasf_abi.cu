@@ -376,6 +376,12 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
                      (int)p.tile_groups.size() + (p.tctamap.empty() ? 0 : 1) +
                      (p.ctamap.empty() ? 0 : 1);
   const int nl = (fork && groups > 1) ? std::min<int>(groups, (int)ctx->lanes.size()) : 0;
+  // A plan whose CTAs all fit one per SM runs its tiled kernels one CTA per
+  // SM (the instance with twice the registers).
+  long long plan_ctas = (long long)p.reg_order.size() + (long long)p.order.size() +
+                        (long long)p.tctamap.size() + (long long)p.ctamap.size();
+  for (const auto& kv : p.tile_groups) plan_ctas += (long long)kv.first * kv.second.size();
+  const bool alone = plan_ctas <= ctx->num_sms;
   cudaEvent_t ev_fork = nullptr;
   if (nl > 0) {
     e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
@@ -411,7 +417,7 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
     for (auto it = at_of.rbegin(); it != at_of.rend(); ++it) {
       const auto& jobs_of = p.tile_groups.at(it->first);
       e = launch_tile_cluster(d_jobs, (const int*)(base + p.off_order) + it->second,
-                              (int)jobs_of.size(), it->first, lane());
+                              (int)jobs_of.size(), it->first, alone, lane());
       if (e != cudaSuccess) return cuda_status(e);
       ++ctx->launches;
     }
@@ -429,7 +435,7 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
         if (end > at && (int)(end - at) + gsz > ctx->tile_gang_max) break;
         end += gsz;
       }
-      e = launch_tile_gang(d_jobs, d_tmap + at, (int)(end - at), groups == 1, ls);
+      e = launch_tile_gang(d_jobs, d_tmap + at, (int)(end - at), alone, ls);
       if (e != cudaSuccess) return cuda_status(e);
       ++ctx->launches;
       at = end;

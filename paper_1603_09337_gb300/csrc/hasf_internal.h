@@ -127,7 +127,7 @@ int tile_count(int w, int h);
 size_t tile_gang_words(int w, int h);
 int tile_clusters_possible(int csize);
 cudaError_t launch_tile_cluster(const Job* d_jobs, const int* d_order, int njobs, int csize,
-                                cudaStream_t s);
+                                bool alone, cudaStream_t s);
 int max_tile_gang_ctas(int device);
 cudaError_t launch_tile_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, bool alone,
                              cudaStream_t s);

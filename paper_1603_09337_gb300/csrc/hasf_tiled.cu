@@ -14,7 +14,9 @@
 namespace hasf {
 
 // One cluster of ntx * nty CTAs per image: cluster i works on job order[i].
-__global__ void __launch_bounds__(kThreads, 2)
+// MINB as for the gang kernel below.
+template <int MINB>
+__global__ void __launch_bounds__(kThreads, MINB)
 hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ order) {
   extern __shared__ uint4 smem4[];
   uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
@@ -39,8 +41,8 @@ hasf_tile_cluster_kernel(const Job* __restrict__ jobs, const int* __restrict__ o
 }
 
 // Gang mode with tiles: CTA b works on tile ctamap[b].y of job ctamap[b].x.
-// MINB = 2 is the default; a launch that has the GPU to itself and no more
-// tiles than SMs uses MINB = 1 (one CTA per SM with twice the registers).
+// MINB = 2 is the default; a plan whose CTAs all fit one per SM uses
+// MINB = 1 (one CTA per SM with twice the registers, no spills).
 template <int MINB>
 __global__ void __launch_bounds__(kThreads, MINB)
 hasf_tile_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) {
@@ -72,9 +74,9 @@ size_t tile_gang_words(int w, int h) { return (size_t)tile_count(w, h) * kGangTi
 int tile_clusters_possible(int csize) {
   if (csize < 1 || csize > 16) return 0;
   const size_t smem = tile_smem_bytes();
-  cudaFuncSetAttribute(hasf_tile_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(hasf_tile_cluster_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
-  cudaFuncSetAttribute(hasf_tile_cluster_kernel,
+  cudaFuncSetAttribute(hasf_tile_cluster_kernel<2>,
                        cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(csize);
@@ -88,7 +90,7 @@ int tile_clusters_possible(int csize) {
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, hasf_tile_cluster_kernel, &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, hasf_tile_cluster_kernel<2>, &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -96,13 +98,12 @@ int tile_clusters_possible(int csize) {
 }
 
 cudaError_t launch_tile_cluster(const Job* d_jobs, const int* d_order, int njobs, int csize,
-                                cudaStream_t s) {
+                                bool alone, cudaStream_t s) {
   const size_t smem = tile_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(hasf_tile_cluster_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(hasf_tile_cluster_kernel,
-                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  const void* fn = alone ? (const void*)hasf_tile_cluster_kernel<1>
+                         : (const void*)hasf_tile_cluster_kernel<2>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(njobs * csize);
@@ -116,7 +117,8 @@ cudaError_t launch_tile_cluster(const Job* d_jobs, const int* d_order, int njobs
   attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, hasf_tile_cluster_kernel, d_jobs, d_order);
+  void* args[] = {(void*)&d_jobs, (void*)&d_order};
+  return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 int max_tile_gang_ctas(int device) {
