@@ -1,9 +1,10 @@
 // hasf_tiled.cu -- the tiled register kernels (images larger than one tile:
-// thread-block clusters and gangs) and their launchers.  Both kernels are
-// built for two CTAs per SM (64 registers, 93 KB of shared memory: the
-// movable mask is read from the constraint planes in L2 instead of being kept
-// in shared memory): their sweeps wait on exchanges, and a second CTA per SM
-// fills those waits; a gang of more tiles than SMs also fits.
+// thread-block clusters and gangs) and their launchers.  Each kernel has two
+// instances.  MINB = 2 fits two CTAs per SM (64 registers, 93 KB of shared
+// memory: the movable mask is read from the constraint planes instead of being
+// kept in shared memory): the sweeps wait on exchanges, a second CTA per SM
+// fills those waits, and a gang of more tiles than SMs fits.  MINB = 1 (128
+// registers, no spills) serves plans whose CTAs all fit one per SM.
 #include <cstdint>
 #include <cuda_runtime.h>
 
