@@ -613,6 +613,12 @@ def run_hasf(args):
             "frac": achieved / alu_peak, "traffic": _traffic(args.workload),
             "peak_source": "152 SMs x 128 int32 lanes x max SM clock (recipe unit counts)",
             "ops_per_step": ops, "counters": stats}
+    rec_n = _traffic_record(args.workload)
+    if rec_n is not None:
+        # the same kernel's issue-slot and integer-pipe use (ncu): how much of
+        # the issue peak it really occupies, algorithmic work or not
+        roof["ncu_issue_active_pct"] = rec_n.get("issue_active_pct")
+        roof["ncu_alu_pipe_pct"] = rec_n.get("alu_pipe_pct")
     in_bytes = sum(x.numel() for x in Xs) + sum(c.numel() for c in Cs if c is not None)
     alg_bytes = in_bytes + sum(o.numel() for o in outs)
     gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
