@@ -65,11 +65,15 @@ def test_volumes_equal_oracle(ctx, rmax):
 
 
 def test_gang_volume_equals_oracle(ctx):
-    """A volume shared by a gang of several CTAs."""
+    """A volume shared by a gang of several CTAs, with and without C and D."""
     X = balls(7, 40, 48, 70, 12, 3, 7, 0.03)
-    got = host(ctx.smooth3d([(dev(X), 2, None, None)])[0])
+    rng = np.random.default_rng(17)
+    C = (X & (rng.random(X.shape) < 0.02)).astype(np.uint8)
+    D = ((1 - X) & (rng.random(X.shape) < 0.03)).astype(np.uint8)
+    outs = ctx.smooth3d([(dev(X), 2, None, None), (dev(X), 2, dev(C), dev(D))])
     ctx.status()
-    np.testing.assert_array_equal(got, oracle.hasf3d(X, 2))
+    np.testing.assert_array_equal(host(outs[0]), oracle.hasf3d(X, 2))
+    np.testing.assert_array_equal(host(outs[1]), oracle.hasf3d(X, 2, C=C, D=D))
 
 
 def test_round_cap_reports_timeout(ctx):
