@@ -270,6 +270,13 @@ def test_host_buffers_pinned_mapped_and_staged(ctx):
             np.testing.assert_array_equal(bo[:, :w], oracle.hasf(X, r, C=C, conn=cn))
             assert (bo[:, w:] == 7).all()
     ctx.set_option(_lib.OPT_HOST_MAPPED, 1)
+    # rows of whole 16-byte chunks: the copy kernel's vector path
+    wide = [case_image(400 + i, 96 + 64 * i, 512 - 128 * i) for i in range(3)]
+    hw = [torch.from_numpy(x).pin_memory().numpy() for x in wide]
+    hwo = [torch.from_numpy(np.zeros_like(x)).pin_memory().numpy() for x in wide]
+    ctx.smooth_host([(x, 2, None, None, 8, o) for x, o in zip(hw, hwo)])
+    for x, o in zip(wide, hwo):
+        np.testing.assert_array_equal(o, oracle.hasf(x, 2))
     # forty pinned images in one call
     xs = [case_image(300 + i, 40 + i, 70 - i) for i in range(40)]
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
