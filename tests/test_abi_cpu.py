@@ -85,3 +85,21 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, option numbers and HASF_RMAX_STABLE in the Python binding
+    equal the header's."""
+    from paper_1603_09337_gb300 import _lib
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {m.group(1): int(m.group(2))
+              for m in re.finditer(r"\b(HASF_[A-Z_0-9]+)\s*=\s*(-?\d+)", text)}
+    m = re.search(r"#define\s+HASF_RMAX_STABLE\s+\(?(-?\d+)\)?", text)
+    assert m and int(m.group(1)) == _lib.RMAX_STABLE
+    checked = 0
+    for name, value in consts.items():
+        py = name[len("HASF_"):] if name.startswith("HASF_OPT_") else name
+        if hasattr(_lib, py):
+            assert getattr(_lib, py) == value, name
+            checked += 1
+    assert checked >= 18
