@@ -199,8 +199,9 @@ bool wants_gang(const hasf_ctx* ctx, const hasf_image& im) {
   return it != ctx->tune.end() && it->second > 0 && !reg_kernel_ok(im.width, im.height, im.rmax);
 }
 bool uses_reg(const hasf_ctx* ctx, const hasf_image& im) {
-  return !ctx->opt.force_gang && !ctx->opt.generic_only && im.rmax > 0 &&
-         reg_kernel_ok(im.width, im.height, im.rmax);
+  // a run to stability (rmax < 0) takes the register kernel when its cap fits
+  return !ctx->opt.force_gang && !ctx->opt.generic_only &&
+         reg_kernel_ok(im.width, im.height, im.rmax < 0 ? -im.rmax : im.rmax);
 }
 
 int gang_size(const hasf_ctx* ctx, const hasf_image& im) {

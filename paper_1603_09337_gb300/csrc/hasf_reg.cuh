@@ -390,12 +390,36 @@ __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
     return reg_operator<CONN, true>(k, S, r, nullptr, jb.g0);
   };
   switch (jb.op) {
-    case OP_HASF:
+    case OP_HASF: {
+      // run to stability: keep the image before each step in g1 and stop
+      // after the first step that leaves it unchanged
+      bool fixed = false;
       for (int r = jb.r_lo; ok && r <= jb.r_hi; ++r) {
+        if (jb.stable) {
+#pragma unroll
+          for (int q = 0; q < kRegR; ++q) {
+            const int y = k.s0 + q;
+            if (y < g.h && k.jin) jb.g1[y * g.wpr + k.j] = S[q];
+          }
+        }
         ok = hc(r);
         if (ok) ok = hf(r);
+        if (ok && jb.stable) {
+          int d = 0;
+#pragma unroll
+          for (int q = 0; q < kRegR; ++q) {
+            const int y = k.s0 + q;
+            if (y < g.h && k.jin) d |= jb.g1[y * g.wpr + k.j] != S[q];
+          }
+          if (!__syncthreads_or(d)) {
+            fixed = true;
+            break;
+          }
+        }
       }
+      if (ok && jb.stable && !fixed && threadIdx.x == 0) atomicMax(jb.status, (int)DEV_UNSTABLE);
       break;
+    }
     case OP_THIN: ok = reg_operator<CONN, true>(k, S, jb.r_hi, nullptr, jb.cp); break;
     case OP_THICK: ok = reg_operator<CONN, false>(k, S, jb.r_hi, jb.cp, nullptr); break;
     case OP_HC: ok = hc(jb.r_hi); break;

@@ -127,3 +127,24 @@ def test_stable_rejected_where_undefined(ctx):
         ctx.smooth(X, 0)
     with pytest.raises(_lib.HasfError):
         ctx.operator(_lib.OP_THIN, X, -3)
+
+
+@pytest.mark.parametrize("conn", [8, 4])
+def test_stable_on_the_register_kernel(ctx, conn):
+    """Caps of at most 31 steps on images of at most 512 x 512 run on the
+    register kernel; the results equal the oracle's."""
+    jobs, expect = [], []
+    for i, (h, w) in enumerate([(40, 48), (80, 96), (128, 130), (300, 512), (512, 257)]):
+        X = img(1900 + i, h, w)
+        C = synth.constraint_points(i, X, 5) if i % 2 else None
+        out, r = oracle.hasf_stable(X, 31, C=C, conn=conn)
+        jobs.append(Image(dev(X), -31, C=None if C is None else dev(C), conn=conn))
+        expect.append((out, r))
+    outs = ctx.smooth_batch(jobs)
+    if all(r > 0 for _, r in expect):
+        ctx.status()
+    else:
+        with pytest.raises(_lib.HasfError):
+            ctx.status()
+    for o, (e, _) in zip(outs, expect):
+        np.testing.assert_array_equal(host(o), e)
