@@ -80,8 +80,9 @@ typedef enum {
  * HC_r^C then HF_r^D) until one leaves the image unchanged, at most -rmax
  * steps.  out receives the image after the last step run; if step -rmax still
  * changed it, the job's status is HASF_EUNSTABLE (reported like
- * HASF_ETIMEOUT; a timeout takes precedence).  Such images run on the generic
- * kernels, with one more h * ceil(w / 32)-word plane of scratch. */
+ * HASF_ETIMEOUT; a timeout takes precedence).  Such images run on the
+ * register kernel when they are at most 512 x 512 and -rmax <= 31, else on the
+ * generic kernels, with one more h * ceil(w / 32)-word plane of scratch. */
 typedef struct hasf_image {
     const uint8_t *in;
     uint8_t *out;
