@@ -167,6 +167,17 @@ def test_operators3d_are_ultimate():
         assert not oracle.simple3d(code_at(G, z, y, x))
 
 
+def test_ultimate_thinning_of_a_box_is_one_voxel():
+    """A solid box (collapsible) thinned with nothing kept ends as one voxel."""
+    rng = np.random.default_rng(23)
+    for _ in range(4):
+        d, h, w = (int(v) for v in rng.integers(2, 7, size=3))
+        X = np.zeros((d + 2, h + 2, w + 3), np.uint8)
+        X[1:1 + d, 1:1 + h, 1:1 + w] = 1
+        T = oracle.operator3d(X, np.zeros_like(X), 6, True)
+        assert T.sum() == 1 and (T <= X).all()
+
+
 def test_hand_worked_thinning_of_a_2x2x2_block():
     """H(block, empty) of the block (0..1)^3: every voxel has priority 1; the
     round visits subfields (x, y, z) parities (0,0,0), (1,0,0), (0,1,0),

@@ -124,6 +124,23 @@ def test_thin_invariants(conn):
 
 
 @pytest.mark.parametrize("conn", [8, 4])
+def test_ultimate_thinning_of_a_simply_connected_set_is_one_point(conn):
+    """With W empty, a set that is one component with a connected complement
+    thins down to a single point (2D: such a set is reducible to a point by
+    simple deletions, and the thinning stops only when no point is simple)."""
+    used = 0
+    for seed in range(12):
+        Z = synth.shapes_image(seed + 300, 30, 26, 1 + seed % 2, 3, 9, n_holes=0, jitter=0,
+                               noise_permille=0)
+        if B.component_counts(Z, conn) != (1, 1):
+            continue
+        used += 1
+        res = oracle.thin(Z, np.zeros_like(Z), _prio_thin(Z), conn)
+        assert res.sum() == 1 and (res <= Z).all()
+    assert used >= 3
+
+
+@pytest.mark.parametrize("conn", [8, 4])
 def test_thicken_invariants(conn):
     """Y within *H(Y,V) within Y cup V; same topology; no point of V left that
     could still be added."""
