@@ -23,10 +23,13 @@
  *  - Adjacency pair (n, nbar) is (8,4) or (4,8) (Sec. 2); "conn" is n.
  *
  * Parity status: every function is pinned by the CPU tests (brute force,
- * global topology, closed forms, invariants, a hand-worked example) except
- * hasf_oracle_hasf as a whole on the paper's own images, which the paper does
- * not print: that whole-filter comparison is "parity unpinned" beyond the
- * invariants and closed forms.
+ * global topology, closed forms, invariants, hand-worked examples).  The
+ * composition of the whole filter (radii ascending, cutting before filling)
+ * is pinned by the classical alternating sequential filter by disc unions,
+ * which it equals on simply connected shapes, and by a hand-worked HASF_1
+ * example on which the two orders of HC_1 and HF_1 differ.  The paper prints
+ * no result of the filter on its own images, so no comparison with those
+ * exists.
  */
 #include <stdint.h>
 #include <stdlib.h>

@@ -213,10 +213,10 @@ def _read_golden(path):
         if line.startswith("name:"):
             cur = {"name": line.split(":", 1)[1].strip()}
             blocks.append(cur)
-        elif line.split(":")[0] in ("op", "cite"):
+        elif line.split(":")[0] in ("op", "cite", "rmax"):
             k, v = line.split(":", 1)
             cur[k] = v.strip()
-        elif line in ("input:", "expected:"):
+        elif line in ("input:", "expected:", "swapped:"):
             key = line[:-1]
             cur[key] = []
         else:
@@ -237,6 +237,26 @@ def test_hand_worked_examples():
             V = ((grid == "v") | (grid == "#")).astype(np.uint8)
             res = oracle.thicken(S, V, B.edt_brute(S))
         np.testing.assert_array_equal(res, exp, err_msg=b["name"])
+
+
+def _grid(rows):
+    return (np.array([list(r) for r in rows]) == "#").astype(np.uint8)
+
+
+def test_hand_worked_hasf1_order():
+    """HASF_1 = HF_1 o HC_1 (cutting first): on the worked example the filter
+    gives the hand-derived image, and the operators applied the other way
+    round give the other hand-derived image."""
+    blocks = _read_golden(os.path.join(GOLDEN, "hasf1_order.txt"))
+    assert blocks
+    for b in blocks:
+        assert b["op"] == "hasf"
+        X, want, other = _grid(b["input"]), _grid(b["expected"]), _grid(b["swapped"])
+        r = int(b["rmax"])
+        assert (want != other).any()
+        np.testing.assert_array_equal(oracle.hasf(X, r), want, err_msg=b["name"])
+        np.testing.assert_array_equal(oracle.hf(oracle.hc(X, r), r), want, err_msg=b["name"])
+        np.testing.assert_array_equal(oracle.hc(oracle.hf(X, r), r), other, err_msg=b["name"])
 
 
 # --- cutting, filling, HASF (Sec. 2, eqs. (i), (ii)) ---------------------------
@@ -304,6 +324,84 @@ def test_filling_is_closing_on_trivial_shapes(r):
         changed += int((Wx != X).any())
         np.testing.assert_array_equal(oracle.hf(X, r), Wx)
     assert used >= 20 and changed >= 10
+
+
+def _spur_shapes():
+    """A block with 2-4 spurs (width 1-3, length 3-8) and 1-3 notches (width
+    1-3, depth 2-6) on its sides: features of every size from 1 to 3, so
+    that openings and closings of different radii, and their order, matter."""
+    out = []
+    for seed in range(48):
+        rng = synth.SplitMix64(seed + 7000)
+        img = np.zeros((56, 60), np.uint8)
+        y0, x0 = rng.randint(10, 16), rng.randint(10, 16)
+        y1, x1 = rng.randint(36, 44), rng.randint(38, 48)
+        img[y0:y1, x0:x1] = 1
+        for val, count in ((1, rng.randint(2, 5)), (0, rng.randint(1, 4))):
+            for _ in range(count):
+                wd = rng.randint(1, 3)
+                ln = rng.randint(3, 8) if val else rng.randint(2, 6)
+                side = rng.randint(0, 3)
+                if side < 2:
+                    p = rng.randint(x0 + 2, x1 - 6)
+                    ys = (slice(y0 - ln, y0) if side == 0 else slice(y1, y1 + ln)) if val else \
+                         (slice(y0, y0 + ln) if side == 0 else slice(y1 - ln, y1))
+                    img[ys, p:p + wd] = val
+                else:
+                    p = rng.randint(y0 + 2, y1 - 6)
+                    xs = (slice(x0 - ln, x0) if side == 2 else slice(x1, x1 + ln)) if val else \
+                         (slice(x0, x0 + ln) if side == 2 else slice(x1 - ln, x1))
+                    img[p:p + wd, xs] = val
+        out.append(img)
+    return out
+
+
+def _alternating(X, steps):
+    """The classical alternating filter by explicit disc unions: for each
+    ("open" | "close", r) in order, gamma_r(Y) = delta_r(eps_r(Y)) or
+    phi_r(Y) = eps_r(delta_r(Y)) cup Y.  None unless every step meets the
+    conditions under which HC_r = gamma_r and HF_r = phi_r (the sets involved
+    are each one component with a connected complement; see the two tests
+    above)."""
+    Y = X.copy()
+    for kind, r in steps:
+        if kind == "open":
+            E, G = B.erode_union(Y, r), B.opening(Y, r)
+            if not (B.is_simply_connected(Y) and E.any() and B.is_simply_connected(E)
+                    and B.is_simply_connected(G)):
+                return None
+            Y = G
+        else:
+            Wx = B.erode_union(B.dilate_union(Y, r), r) | Y
+            if not (B.is_simply_connected(Y) and B.is_simply_connected(B.dilate_union(Y, r))
+                    and B.is_simply_connected(Wx)):
+                return None
+            Y = Wx
+    return Y.astype(np.uint8)
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_hasf_is_the_alternating_filter_on_trivial_shapes(n):
+    """HASF_n = HF_n o HC_n o ... o HF_1 o HC_1 (Sec. 2), read right to left:
+    radii ascending, cutting before filling.  Where every intermediate set is
+    one component with a connected complement, each HC_r is the opening and
+    each HF_r the closing cup Y, so HASF_n(X) is the alternating sequential
+    filter phi_n gamma_n ... phi_1 gamma_1 (X) computed by disc unions.  The
+    shapes are chosen so that the other orders (filling first, or radii
+    descending) give other images: a filter composed that way fails here."""
+    used = swapped_differs = descending_differs = 0
+    for X in _spur_shapes():
+        want = _alternating(X, [(k, r) for r in range(1, n + 1) for k in ("open", "close")])
+        if want is None:
+            continue
+        used += 1
+        np.testing.assert_array_equal(oracle.hasf(X, n), want)
+        sw = _alternating(X, [(k, r) for r in range(1, n + 1) for k in ("close", "open")])
+        de = _alternating(X, [(k, r) for r in range(n, 0, -1) for k in ("open", "close")])
+        swapped_differs += sw is not None and bool((sw != want).any())
+        descending_differs += de is not None and bool((de != want).any())
+    assert used >= 30 and swapped_differs >= 10 and descending_differs >= 10, \
+        (used, swapped_differs, descending_differs)
 
 
 def test_open_and_closed_image_is_a_fixed_point():
