@@ -35,43 +35,41 @@ BATCH = 256
 RMAX = 5
 WORKLOAD = ("batch of 256 synthetic 512x512 binary images (discs/ellipses, holes, jitter, "
             "2-10% salt-and-pepper), rmax=5, 50 kept points C per image, one batched launch")
-# Algorithmic lane operations (32 pixels per lane) of the bit-sliced method:
-# one word test = 6 funnel shifts aligning the 8 neighbours, 8 for the four
-# crossing terms, 4 to count exactly one, 2 to gate by the candidates and
-# update the set; one ring read of a level update = 1 funnel shift + 1 OR.
-OPS_PER_WORD_TEST = 20
-OPS_PER_RING_EVAL = 2
+# Algorithmic lane operations (32 pixels per lane) of the bit-sliced method
+# (RECIPE_MIX below): one word test = 6 funnel shifts aligning the 8
+# neighbours, 8 logic operations for the four crossing terms, 4 to count
+# exactly one, 2 to gate by the candidates and update the set; one ring read
+# of a level update = 1 funnel shift + 1 OR.
 # 3D: one voxel test = 27 lane-ops to assemble the 27-bit neighbourhood plus
 # at least two dilation steps of each of the two flood fills (about 18 each),
 # counted as 100; one ring read of a word = funnel shift + AND/OR + address, 4.
 OPS_PER_VOXEL_TEST = 100
 OPS_PER_RING3_EVAL = 4
-SM_COUNT = 152
 INT32_LANES_PER_SM = 128
+# Lane-operations of the recipe by instruction class: per word test 6 funnel
+# shifts and 14 logic operations, per ring read 1 funnel shift and 1 OR.
+RECIPE_MIX = {"word_tests": {"shf": 6, "lop3": 14}, "ring_evals": {"shf": 1, "lop3": 1}}
+
+
+TRAFFIC_SOURCES = ("hasf_reg.cu", "hasf_reg.cuh", "hasf_device.cuh", "hasf_internal.h")
 
 
 def _traffic_record(workload: str):
-    """The headline kernel's last ncu capture (DRAM and L2 bytes per launch),
-    if the kernel sources are still the ones that capture measured."""
+    """(record, stale): the headline kernel's last ncu capture (DRAM and L2
+    bytes per launch) and whether the kernel sources have changed since it
+    was taken (then the record is not used)."""
     import hashlib
     if workload != "batch512":
-        return None
+        return None, False
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "hasf_reg_kernel_traffic.json")))
-        src = b"".join(open(os.path.join(ROOT, "paper_1603_09337_gb300", "csrc", f), "rb").read()
-                       for f in ("hasf_reg.cu", "hasf_reg.cuh", "hasf_device.cuh",
-                                 "hasf_internal.h"))
-        if hashlib.sha256(src).hexdigest()[:16] != rec["source_sha256_16"]:
-            return None
-        return rec
     except Exception:
-        return None
-
-
-def _traffic(workload: str):
-    """DRAM bytes per launch of the headline kernel (ncu), or None."""
-    rec = _traffic_record(workload)
-    return None if rec is None else rec["dram_bytes_read"] + rec["dram_bytes_write"]
+        return None, False
+    src = b"".join(open(os.path.join(ROOT, "paper_1603_09337_gb300", "csrc", f), "rb").read()
+                   for f in TRAFFIC_SOURCES)
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
+        return None, True
+    return rec, False
 
 
 def _cpu_model() -> str:
@@ -90,6 +88,50 @@ def _cpu_model() -> str:
     except Exception:
         pass
     return "unknown"
+
+
+def measured_int_peaks(device: int):
+    """Lane-operations per second of each integer instruction class on this
+    GPU, from the probe kernels of libhasf_peak.so (CUDA events)."""
+    import ctypes
+    from paper_1603_09337_gb300 import build
+    lib = ctypes.CDLL(build.PEAK_LIB)
+    lib.hasf_peak_int.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_float)]
+    out = {}
+    for k, name in enumerate(("lop3", "shf", "iadd3", "shfl")):
+        best = 0.0
+        for _ in range(3):
+            v, ms = ctypes.c_double(), ctypes.c_float()
+            if lib.hasf_peak_int(k, device, ctypes.byref(v), ctypes.byref(ms)) == 0:
+                best = max(best, v.value)
+        out[name] = best / 1e12 if best else None
+    return out
+
+
+def alu_roofline(stats, ms_per_step, sms, sm_max_mhz, peaks_t):
+    """The recipe's lane-operations per step over the step time, against the
+    measured rate of its instruction mix (the time the recipe would take if
+    every class ran at its measured rate, one after another)."""
+    n = {"shf": 0, "lop3": 0}
+    for key, mix in RECIPE_MIX.items():
+        for cls, per in mix.items():
+            n[cls] += stats[key] * per
+    ops = sum(n.values())
+    achieved = ops / (ms_per_step / 1e3) / 1e12
+    nominal = sms * INT32_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "unit": "Tops/s", "ops_per_step": ops,
+            "counters": stats, "peak_nominal": nominal,
+            "peak_nominal_source": f"{sms} SMs x 128 int32 lanes x {sm_max_mhz:.0f} MHz"}
+    if peaks_t and all(peaks_t.get(c) for c in n):
+        t_min = sum(n[c] / (peaks_t[c] * 1e12) for c in n)
+        roof.update(peak=ops / t_min / 1e12, frac=achieved / (ops / t_min / 1e12),
+                    peak_source="measured: per-class integer probe rates (hasf_peak_int) "
+                                "weighted by the recipe's mix of funnel shifts and logic",
+                    measured_class_peaks_tops=peaks_t)
+    else:
+        roof.update(peak=nominal, frac=achieved / nominal, peak_source="nominal (probe failed)")
+    return roof
 
 
 def _peaks():
@@ -250,7 +292,7 @@ def serving_pool(n: int = 48, seed: int = 4):
     return out
 
 
-def run_serving(ctx, dev, seconds: float, rate: float = 2000.0):
+def run_serving(ctx, dev, seconds: float, rate: float = 2000.0, seq_limit_s: float = 10.0):
     """Served stream vs plain sequential launches; latency = completion - arrival."""
     import numpy as np
     import torch
@@ -325,7 +367,7 @@ def run_serving(ctx, dev, seconds: float, rate: float = 2000.0):
         return lat, time.perf_counter() - t0
 
     s_lat, s_wall = served()
-    q_lat, q_wall = sequential(seconds * 2)
+    q_lat, q_wall = sequential(seq_limit_s)
     pct = lambda a, p: float(np.percentile(np.array(a) * 1e3, p)) if a else None
     mpx = sum(pool[picks[q]].size for q in range(n)) / 1e6
     return {
@@ -338,6 +380,50 @@ def run_serving(ctx, dev, seconds: float, rate: float = 2000.0):
                                 "images_per_s": len(q_lat) / q_wall,
                                 "completed": len(q_lat)},
     }
+
+
+def single_image_latency(ctx, dev, flush, stream, reps: int = 50):
+    """Latency of the single-image workload (512 x 512, 12 shapes, 6 holes,
+    5 % noise, rmax 3, no C): CUDA events around each hasf_smooth call on
+    `stream`, and around each hasf_smooth_noalloc call."""
+    import ctypes
+    import torch
+    from paper_1603_09337_gb300 import _lib, synth
+    job = synth.single_512()
+    x = torch.from_numpy(job.X).to(dev)
+    out = torch.empty_like(x)
+    lib = _lib.load()
+    d = _lib.HasfImage(x.data_ptr(), out.data_ptr(), None, None, 512, 512, 512, job.rmax, 8, 0)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    calls = {
+        "hasf_smooth": lambda: ctx.smooth(x, job.rmax, out=out),
+        "hasf_smooth_noalloc": lambda: _lib.check(
+            lib.hasf_smooth_noalloc(ctypes.byref(d), ctypes.c_void_p(st.data_ptr()),
+                                    ctypes.c_void_p(stream.cuda_stream)), "noalloc"),
+    }
+    res = {"workload": "one 512x512 image (12 shapes, 6 holes, 2-px jitter, 5% noise), rmax=3, "
+                       "no C, one call", "reps": reps,
+           "l2": "flushed before each call (untimed)"}
+    with ClockSampler(dev.index or 0) as clk:
+        for name, call in calls.items():
+            for _ in range(5):
+                call()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                call()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            ctx.status()
+            res[name] = {"best_ms": min(ts), "median_ms": statistics.median(ts),
+                         "images_per_s": 1e3 / statistics.median(ts)}
+    res["clocks"] = clk.summary()
+    return res
 
 
 def run_volume(args):
@@ -416,7 +502,8 @@ def run_volume(args):
         return 0
     peaks, peak_src = _peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SM_COUNT * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sms * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12
     ops = stats["word_tests"] * OPS_PER_VOXEL_TEST + stats["ring_evals"] * OPS_PER_RING3_EVAL
     achieved = ops / (ms_per_step / 1e3) / 1e12
     vox = sum(x.numel() for x in Xs)
@@ -439,7 +526,7 @@ def run_volume(args):
                    "l2": "flushed between timed steps (256 MB write, untimed)", "wall_s": wall},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": None,
-                     "peak_source": "152 SMs x 128 int32 lanes x max SM clock (recipe unit counts)",
+                     "peak_source": f"{sms} SMs x 128 int32 lanes x max SM clock (nominal)",
                      "ops_per_step": ops, "counters": stats},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
     }
@@ -573,6 +660,17 @@ def run_hasf(args):
         per_image = {"value": n * ws / (tp / 1e3), "unit": "images/s", "ms_per_step": tp,
                      "launches_per_step": n, "steps": k}
 
+    # The single-image workload: one 512 x 512 image, rmax 3, one launch --
+    # a latency figure (best and median of 50 launches after warm-up, L2
+    # flushed before each), through hasf_smooth and through the
+    # allocation-free entry point.
+    single = None
+    if args.workload == "batch512" and rank == 0:
+        single = single_image_latency(ctx, dev, flush, stream)
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    int_peaks = measured_int_peaks(local)
+
     # End to end through the host-buffer entry point with pinned host buffers:
     # H2D of X and C, the smoothing, D2H of the result, every step.
     e2e = None
@@ -597,7 +695,7 @@ def run_hasf(args):
 
     serving = None
     if rank == 0 and args.serve_seconds > 0 and args.workload == "batch512":
-        serving = run_serving(ctx, dev, args.serve_seconds)
+        serving = run_serving(ctx, dev, args.serve_seconds, seq_limit_s=args.sequential_seconds)
 
     if rank != 0:
         ctx.close()
@@ -606,24 +704,22 @@ def run_hasf(args):
     peaks, peak_src = _peaks()
     clocks = clk.summary()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = SM_COUNT * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12      # T lane-ops/s
-    ops = stats["word_tests"] * OPS_PER_WORD_TEST + stats["ring_evals"] * OPS_PER_RING_EVAL
-    achieved = ops / (ms_per_step / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-            "frac": achieved / alu_peak, "traffic": _traffic(args.workload),
-            "peak_source": "152 SMs x 128 int32 lanes x max SM clock (recipe unit counts)",
-            "ops_per_step": ops, "counters": stats}
-    rec_n = _traffic_record(args.workload)
-    if rec_n is not None:
+    roof = alu_roofline(stats, ms_per_step, sms, sm_max, int_peaks)
+    rec, stale = _traffic_record(args.workload)
+    roof["traffic"] = None if rec is None else rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    if stale:
+        roof["traffic_stale"] = True   # the ncu record predates the kernel sources timed here
+    if rec is not None:
         # the same kernel's issue-slot and integer-pipe use (ncu): how much of
         # the issue peak it really occupies, algorithmic work or not
-        roof["ncu_issue_active_pct"] = rec_n.get("issue_active_pct")
-        roof["ncu_alu_pipe_pct"] = rec_n.get("alu_pipe_pct")
+        roof["ncu_issue_active_pct"] = rec.get("issue_active_pct")
+        roof["ncu_alu_pipe_pct"] = rec.get("alu_pipe_pct")
+        roof["ncu_warps_active"] = rec.get("warps_active")
     in_bytes = sum(x.numel() for x in Xs) + sum(c.numel() for c in Cs if c is not None)
     alg_bytes = in_bytes + sum(o.numel() for o in outs)
     gbs = alg_bytes / (ms_per_step / 1e3) / 1e9
-    rec = _traffic_record(args.workload)
     hbm = {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+           "traffic_stale": stale,
            "ncu_dram_bytes_per_launch": None if rec is None else
            rec["dram_bytes_read"] + rec["dram_bytes_write"],
            "ncu_l2_bytes_per_launch": None if rec is None else rec.get("lts_bytes"),
@@ -669,7 +765,7 @@ def run_hasf(args):
                    "launch": "CUDA graph replay" if args.graph else "hasf_smooth_batch",
                    "mpixel_per_s": px * args.steps * ws / (t_ms / 1e3) / 1e6, "wall_s": wall},
         "roofline": roof, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e,
-        "per_image_launches": per_image, "serving": serving,
+        "per_image_launches": per_image, "single_image": single, "serving": serving,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -690,7 +786,10 @@ def main():
                     choices=["batch512", "ragged", "large", "volume"])
     ap.add_argument("--ragged-n", type=int, default=1024)
     ap.add_argument("--side", type=int, default=4096)
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--sequential-seconds", type=float, default=10.0,
+                    help="time limit of the plain sequential launches the served stream is "
+                         "compared with")
     ap.add_argument("--graph", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -321,9 +321,11 @@ int hasf_levels(hasf_ctx *ctx, const uint8_t *feat, int32_t width, int32_t heigh
  * It calls no cudaMalloc, cudaFree or other allocating routine.
  *
  * Limit: height * ceil(width / 32) <= 20480 and the image's three bit planes
- * must fit one CTA's shared memory (about 1100 rows at 512 columns, 560 rows at
- * 1024 columns); larger images return HASF_EBUDGET.  Other argument errors
- * return HASF_EINVAL, as for hasf_smooth.
+ * must fit one CTA's shared memory (about 1130 rows at 512 columns, 560 rows at
+ * 1024 columns); larger images return HASF_EBUDGET.  rmax must lie in
+ * [1, 64]: the run to stability that hasf_smooth offers for rmax < 0 is not
+ * available here (it needs one more plane), and such an rmax returns
+ * HASF_EINVAL, like the other argument errors of hasf_smooth.
  *
  * `status` is an optional DEVICE int: it is cleared on `stream` and then
  * receives 0, or HASF_ETIMEOUT if the device iteration cap was hit (NULL: the

@@ -3,6 +3,8 @@
 Each .cu file under csrc/ is compiled in parallel by nvcc with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo``, then the objects are
 linked into one shared library that exports the C ABI of include/hasf.h.
+The benchmark's integer-throughput probe (peak/int_peak.cu, include/hasf_peak.h)
+is built beside it as _build/libhasf_peak.so.
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libhasf.so")
+PEAK_SRC = os.path.join(PKG, "peak", "int_peak.cu")
+PEAK_LIB = os.path.join(OUT_DIR, "libhasf_peak.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
@@ -36,11 +40,11 @@ def sources() -> list[str]:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAK_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAK_LIB))
     deps = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
-    deps += glob.glob(os.path.join(INCLUDE, "*.h"))
+    deps += glob.glob(os.path.join(INCLUDE, "*.h")) + [PEAK_SRC]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
@@ -63,13 +67,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return obj
 
     with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+        objs = list(ex.map(compile_one, sources() + [PEAK_SRC]))
+    peak_obj = objs.pop()
+    for out, parts in ((LIB, objs), (PEAK_LIB, [peak_obj])):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *parts, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, out)
     return LIB
 
 

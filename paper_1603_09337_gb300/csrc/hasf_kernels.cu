@@ -123,52 +123,62 @@ __global__ void levels_walk_kernel(int w, int h, int mode, int r, const uint32_t
 // Host side.
 // ---------------------------------------------------------------------------
 
-cudaError_t upload_level_table() {
-  static LevelTable tab;
-  static bool built = false;
-  if (!built) {
-    // Sort the lattice vectors of the disc of radius kMaxR by squared norm.
-    int n = 0;
-    const int R = kMaxR;
-    static int norms[kMaxOffsets];
-    static int8_t vecs[kMaxOffsets][2];
-    for (int dy = -R; dy <= R; ++dy)
-      for (int dx = -R; dx <= R; ++dx) {
-        const int q = dx * dx + dy * dy;
-        if (q == 0 || q > R * R) continue;
-        norms[n] = q;
-        vecs[n][0] = (int8_t)dx;
-        vecs[n][1] = (int8_t)dy;
-        ++n;
-      }
-    // counting sort by norm (stable)
-    static int count[kMaxR * kMaxR + 2];
-    for (int i = 0; i <= R * R + 1; ++i) count[i] = 0;
-    for (int i = 0; i < n; ++i) ++count[norms[i] + 1];
-    for (int i = 1; i <= R * R + 1; ++i) count[i] += count[i - 1];
-    static int pos[kMaxR * kMaxR + 2];
-    for (int i = 0; i <= R * R + 1; ++i) pos[i] = count[i];
-    for (int i = 0; i < n; ++i) {
-      const int p = pos[norms[i]]++;
-      tab.off[p][0] = vecs[i][0];
-      tab.off[p][1] = vecs[i][1];
+namespace {
+// The host copy of the level table, built once (std::call_once: contexts and
+// the allocation-free entry point may upload it from several threads).
+LevelTable g_level_tab;
+bool g_level_tab_ok = false;
+std::once_flag g_level_tab_once;
+
+void build_level_table() {
+  LevelTable& tab = g_level_tab;
+  // Sort the lattice vectors of the disc of radius kMaxR by squared norm.
+  int n = 0;
+  const int R = kMaxR;
+  static int norms[kMaxOffsets];
+  static int8_t vecs[kMaxOffsets][2];
+  for (int dy = -R; dy <= R; ++dy)
+    for (int dx = -R; dx <= R; ++dx) {
+      const int q = dx * dx + dy * dy;
+      if (q == 0 || q > R * R) continue;
+      norms[n] = q;
+      vecs[n][0] = (int8_t)dx;
+      vecs[n][1] = (int8_t)dy;
+      ++n;
     }
-    int nl = 0;
-    for (int q = 1; q <= R * R; ++q) {
-      if (count[q + 1] == count[q]) continue;
-      tab.value[nl] = (uint16_t)q;
-      tab.start[nl] = (uint16_t)count[q];
-      ++nl;
-    }
-    tab.start[nl] = (uint16_t)n;
-    for (int r = 0; r <= R; ++r) {
-      int c = 0;
-      while (c < nl && tab.value[c] <= r * r) ++c;
-      tab.nlev[r] = (uint16_t)c;
-    }
-    built = (n == kMaxOffsets && nl == kMaxLevels);
-    if (!built) return cudaErrorInvalidValue;
+  // counting sort by norm (stable)
+  static int count[kMaxR * kMaxR + 2];
+  for (int i = 0; i <= R * R + 1; ++i) count[i] = 0;
+  for (int i = 0; i < n; ++i) ++count[norms[i] + 1];
+  for (int i = 1; i <= R * R + 1; ++i) count[i] += count[i - 1];
+  static int pos[kMaxR * kMaxR + 2];
+  for (int i = 0; i <= R * R + 1; ++i) pos[i] = count[i];
+  for (int i = 0; i < n; ++i) {
+    const int p = pos[norms[i]]++;
+    tab.off[p][0] = vecs[i][0];
+    tab.off[p][1] = vecs[i][1];
   }
+  int nl = 0;
+  for (int q = 1; q <= R * R; ++q) {
+    if (count[q + 1] == count[q]) continue;
+    tab.value[nl] = (uint16_t)q;
+    tab.start[nl] = (uint16_t)count[q];
+    ++nl;
+  }
+  tab.start[nl] = (uint16_t)n;
+  for (int r = 0; r <= R; ++r) {
+    int c = 0;
+    while (c < nl && tab.value[c] <= r * r) ++c;
+    tab.nlev[r] = (uint16_t)c;
+  }
+  g_level_tab_ok = (n == kMaxOffsets && nl == kMaxLevels);
+}
+}  // namespace
+
+cudaError_t upload_level_table() {
+  std::call_once(g_level_tab_once, build_level_table);
+  if (!g_level_tab_ok) return cudaErrorInvalidValue;
+  const LevelTable& tab = g_level_tab;
   cudaError_t e = cudaMemcpyToSymbol(c_lv, &tab, sizeof(tab));
   if (e == cudaSuccess) e = set_level_table_reg(&tab, sizeof(tab));
   if (e == cudaSuccess) e = set_level_table_tiled(&tab, sizeof(tab));

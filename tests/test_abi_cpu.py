@@ -103,3 +103,16 @@ def test_binding_constants_match_the_header():
             assert getattr(_lib, py) == value, name
             checked += 1
     assert checked >= 18
+
+
+def test_peak_probe_library_exports_its_symbols(lib):
+    """The benchmark's integer-throughput probe (include/hasf_peak.h) is built
+    beside the library and exports what its header declares."""
+    from paper_1603_09337_gb300 import build
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "hasf_peak.h")).read(),
+                  flags=re.S)
+    names = sorted(set(re.findall(r"\b(hasf_[a-z_0-9]+)\s*\(", text)))
+    assert names == ["hasf_peak_int"]
+    plib = ctypes.CDLL(build.PEAK_LIB)
+    for name in names:
+        assert hasattr(plib, name), name

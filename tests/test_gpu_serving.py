@@ -11,8 +11,8 @@ import time
 import numpy as np
 import pytest
 
-import oracle
 from paper_1603_09337_gb300 import _lib, synth
+from tests._oracle_threads import hasf_many
 
 pytestmark = pytest.mark.gpu
 
@@ -75,9 +75,9 @@ def test_served_results_equal_solo_results(torch_cuda):
         torch.cuda.synchronize()
         for o, s in zip(outs, solo):
             np.testing.assert_array_equal(o.cpu().numpy(), s.cpu().numpy())
-        for i in sorted(range(len(jobs)), key=lambda i: jobs[i][0].size)[:4]:
-            np.testing.assert_array_equal(outs[i].cpu().numpy(),
-                                          oracle.hasf(jobs[i][0], jobs[i][1]))
+        want = hasf_many([(X, r, None, None, 8) for X, r in jobs])
+        for i, w in enumerate(want):
+            np.testing.assert_array_equal(outs[i].cpu().numpy(), w, err_msg=f"job {i}")
 
 
 def test_poll_cancel_and_errors(torch_cuda):
