@@ -34,7 +34,7 @@ hasf_reg_kernel(const Job* __restrict__ jobs, const int* __restrict__ order, int
     g.F = smem + 1 + kRegPadR * g.P;
     g.cand = nullptr;
     g.cap = jb.cap;
-    g.n_tests = g.n_ring = g.n_passes = g.n_levels = g.n_rounds = 0;
+    if (threadIdx.x < STAT_COUNT) s_reg_stats[threadIdx.x] = 0u;  // ordered by the job's first barrier
     k.M = smem + reg_f_words(jb.w, jb.h);
     k.cand = k.M + kRegPlane;
     k.top = k.cand + kRegPlane;

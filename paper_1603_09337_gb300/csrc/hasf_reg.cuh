@@ -51,8 +51,12 @@ __host__ __device__ inline int reg_smem_words(int w, int h) {
 }
 inline size_t reg_smem_bytes(int w, int h) { return (size_t)reg_smem_words(w, h) * 4; }
 
+// Work counters of the CTA's current job (see StatIndex), in shared memory so
+// that they hold no registers: thread 0 or one lane per warp adds to them.
+static __shared__ unsigned s_reg_stats[STAT_COUNT];
+
 struct RegCtx {
-  Ctx<SmemMode> g;      // image geometry (and counters); g.F = F at (row 0, word 0)
+  Ctx<SmemMode> g;      // image geometry; g.F = F at (row 0, word 0)
   uint32_t* M;          // kRegRows rows x kRegPitch words
   uint32_t* cand;       // kRegRows rows x kRegPitch words
   uint32_t* top;        // [warp][kRegW]: first row of each warp
@@ -61,14 +65,57 @@ struct RegCtx {
   bool jin;             // j < words per row of the image
 };
 
+// Three-input logic as one instruction: LUT is the truth table evaluated on
+// a = 0xF0, b = 0xCC, c = 0xAA.
+template <unsigned LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
+
+// Simple-point test of 32 pixels from their eight neighbour planes (bit b of
+// x_k = neighbour k of pixel b, in the order E, NE, N, NW, W, SW, S, SE), by
+// the crossing count of Sec. 2's T = Tbar = 1: with the four terms
+// [x_k = 0 and (x_{k+1} or x_{k+2}) = 1] for k = E, N, W, S (cyclic order),
+// exactly one of them holds.  (4,8) adjacency takes the complemented planes,
+// folded into the terms' truth table.  Nine three-input logic instructions.
+template <int CONN>
+__device__ __forceinline__ uint32_t simple_planes(uint32_t x0, uint32_t x1, uint32_t x2,
+                                                  uint32_t x3, uint32_t x4, uint32_t x5,
+                                                  uint32_t x6, uint32_t x7) {
+  constexpr unsigned T = CONN == 8 ? 0x0Eu : 0x70u;  // ~a & (b | c), or a & ~(b & c)
+  const uint32_t a = lop3<T>(x0, x1, x2), b = lop3<T>(x2, x3, x4);
+  const uint32_t c = lop3<T>(x4, x5, x6), d = lop3<T>(x6, x7, x0);
+  const uint32_t u = a | b, v = c | d;
+  return lop3<0x14u>(a, b, v) | lop3<0x14u>(c, d, u);  // (a ^ b) & ~v | (c ^ d) & ~u
+}
+
+// A row next to the thread's strip (the last row of the strip above, or the
+// first row of the strip below) with its west and east neighbour planes.
+struct EdgeRow {
+  uint32_t v, l, r;
+};
+
 // The two subfield passes (0, SY) then (1, SY) over this thread's rows of
 // parity SY (compile-time).  They are fused row by row: within these two
 // passes a row of parity SY reads only itself and the rows of the other
 // parity (which do not change), so finishing (0, SY) and (1, SY) on one row
-// before the next gives the same result as two full passes.  The simple mask
-// of the first test is reused by the second unless a word of the warp's row
-// changed in between; then only the row's own left/right words are
-// re-shuffled.
+// before the next gives the same result as two full passes.
+//
+// Neighbour planes.  A pixel's west neighbour plane is the row shifted left by
+// one with bit 31 of the word to the left coming in at bit 0; the east plane is
+// the row shifted right with bit 0 of the word to the right coming in at bit
+// 31.  Those cross-word bits come from the packs Wb (bit q = bit 31 of the
+// left neighbour's row q) and Eb (bit 16 + q = bit 0 of the right neighbour's
+// row q), exchanged once per half.  The rows of the other parity do not change
+// in the half, so the planes of row r + 1 (south) serve again as the north of
+// row r + 2.  An even pixel's cross-word neighbours all lie in the left word
+// (bit 31: an odd pixel, unchanged by the first pass); an odd pixel's in the
+// right word (bit 0: an even pixel).  So the second test needs one fresh bit,
+// the right word's updated bit 0 of the row: one shuffle, taken only when the
+// first pass changed a pixel of the row somewhere in the warp (else the first
+// test's result holds for the odd pixels too).
 //
 // `need` (warp-uniform, bit q = row q of either strip of the warp) says which
 // rows can change at all.  A row whose last test left it stable stays stable
@@ -76,55 +123,77 @@ struct RegCtx {
 // no remaining candidate of the row is simple, except that odd-column changes
 // can re-enable even-column candidates of the same row -- then the row stays
 // marked.  A change in row r marks rows r - 1 and r + 1 (the strips of a warp
-// are stacked, so row 15 and row 0 are neighbours across them).  Returns the
-// OR of the changed bits.
-template <int CONN, int SY, bool thin>
-__device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], uint32_t above,
-                                             uint32_t below, uint32_t& need) {
-  const int j = k.j;
-  uint32_t* cr = k.cand + k.s0 * kRegPitch + j;
+// are stacked, so row 15 and row 0 are neighbours across them).  `pack` (bits
+// q and 16 + q: bits 31 and 0 of row q) follows the changes.  Returns the OR
+// of the changed bits.
+template <int CONN, int SY>
+__device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& pack,
+                                             uint32_t Wb, uint32_t Eb, const EdgeRow& xr,
+                                             uint32_t& need) {
+  uint32_t* cr = k.cand + k.s0 * kRegPitch + k.j;
+  const bool jlast = k.j == kRegW - 1;
   uint32_t changed = 0;
   uint32_t rowchg = 0;  // rows of parity SY that changed (made warp-uniform below)
   uint32_t again = 0;   // rows to re-test (odd-column change)
+  uint32_t n = 0, nL = 0, nR = 0;
+  bool nvalid = false;
+  if (SY == 0) {
+    n = xr.v;
+    nL = xr.l;
+    nR = xr.r;
+    nvalid = true;
+  }
 #pragma unroll
   for (int r = SY; r < kRegR; r += 2) {
-    if (!((need >> r) & 1u)) continue;
-    uint32_t cw = cr[r * kRegPitch];
-    if (!__any_sync(0xFFFFFFFFu, cw != 0u)) continue;
-    const uint32_t n = r > 0 ? S[r - 1] : above;
-    uint32_t c = S[r];
-    const uint32_t s = r + 1 < kRegR ? S[r + 1] : below;
-    uint32_t nw = __shfl_up_sync(0xFFFFFFFFu, n, 1, 16);
-    uint32_t wv = __shfl_up_sync(0xFFFFFFFFu, c, 1, 16);
-    uint32_t sw = __shfl_up_sync(0xFFFFFFFFu, s, 1, 16);
-    uint32_t ne = __shfl_down_sync(0xFFFFFFFFu, n, 1, 16);
-    uint32_t e = __shfl_down_sync(0xFFFFFFFFu, c, 1, 16);
-    uint32_t se = __shfl_down_sync(0xFFFFFFFFu, s, 1, 16);
-    if (j == 0) nw = wv = sw = 0u;
-    if (j == kRegW - 1) ne = e = se = 0u;
-    uint32_t sm = simple_bits<CONN>(nw, n, ne, wv, c, e, sw, s, se);
-    const uint32_t chg0 = cw & 0x55555555u & sm;
-    const bool any0 = __any_sync(0xFFFFFFFFu, chg0 != 0u);
-    if (any0) {
-      // odd pixels see only their own word's even pixels on the left, so
-      // only the right neighbour's (updated) word is fetched again
-      c = thin ? (c & ~chg0) : (c | chg0);
-      cw &= ~chg0;
-      e = __shfl_down_sync(0xFFFFFFFFu, c, 1, 16);
-      if (j == kRegW - 1) e = 0u;
-      sm = simple_bits<CONN>(nw, n, ne, wv, c, e, sw, s, se);
+    if (!((need >> r) & 1u)) {
+      nvalid = false;
+      continue;
     }
-    const uint32_t chg1 = cw & 0xAAAAAAAAu & sm;
-    c = thin ? (c & ~chg1) : (c | chg1);
-    cw &= ~chg1;
+    if (!nvalid && r > 0) {  // row r - 1 of the strip
+      n = S[r - 1];
+      nL = __funnelshift_l(Wb << (32 - r), n, 1);
+      nR = __funnelshift_r(n, Eb >> (15 + r), 1);
+    }
+    uint32_t s, sL, sR;
+    if (r + 1 < kRegR) {
+      s = S[r + 1];
+      sL = __funnelshift_l(Wb << (30 - r), s, 1);
+      sR = __funnelshift_r(s, Eb >> (17 + r), 1);
+    } else {
+      s = xr.v;
+      sL = xr.l;
+      sR = xr.r;
+    }
+    uint32_t c = S[r];
+    const uint32_t cw = cr[r * kRegPitch];
+    const uint32_t wl = Wb << (31 - r);
+    uint32_t res = simple_planes<CONN>(__funnelshift_r(c, Eb >> (16 + r), 1), nR, n, nL,
+                                       __funnelshift_l(wl, c, 1), sL, s, sR);
+    const uint32_t chg0 = res & cw & 0x55555555u;
+    if (__any_sync(0xFFFFFFFFu, chg0 != 0u)) {
+      c ^= chg0;  // candidates lie in S for a thinning, outside it for a thickening
+      uint32_t e = __shfl_down_sync(0xFFFFFFFFu, c, 1, 16);
+      if (jlast) e = 0u;
+      res = simple_planes<CONN>(__funnelshift_r(c, e, 1), nR, n, nL, __funnelshift_l(wl, c, 1),
+                                sL, s, sR);
+      rowchg |= 1u << r;
+    }
+    const uint32_t chg1 = res & cw & 0xAAAAAAAAu;
     const uint32_t chg = chg0 | chg1;
     if (chg) {
-      S[r] = c;
-      cr[r * kRegPitch] = cw;
+      S[r] = c ^ chg1;
+      cr[r * kRegPitch] = cw ^ chg;
       changed |= chg;
+      pack ^= ((chg0 << (16 + r)) & (1u << (16 + r))) | ((chg1 >> (31 - r)) & (1u << r));
     }
-    if (any0 || chg1) rowchg |= 1u << r;
-    if (chg1) again |= 1u << r;
+    if (chg1) {
+      rowchg |= 1u << r;
+      again |= 1u << r;
+    }
+    n = s;
+    nL = sL;
+    nR = sR;
+    nvalid = true;
   }
   rowchg = __reduce_or_sync(0xFFFFFFFFu, rowchg);
   again = __reduce_or_sync(0xFFFFFFFFu, again);
@@ -139,23 +208,51 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], ui
   return changed;
 }
 
+// Bits 31 (at bit q) and 0 (at bit 16 + q) of the thread's rows q.
+__device__ __forceinline__ uint32_t edge_pack(const uint32_t (&S)[kRegR]) {
+  uint32_t hb = 0, lb = 0;
+#pragma unroll
+  for (int q = kRegR - 1; q >= 0; --q) hb = __funnelshift_l(S[q], hb, 1);  // (hb << 1) | bit 31
+#pragma unroll
+  for (int q = 0; q < kRegR; ++q) lb = __funnelshift_r(lb, S[q], 1);       // (lb >> 1) | bit 0 << 31
+  return (hb & 0xFFFFu) | (lb & 0xFFFF0000u);
+}
+
+// A row next to the strip with its west / east planes (its neighbours' words
+// come from the lanes beside this one, which hold the same row).
+__device__ __forceinline__ EdgeRow edge_row(uint32_t v, bool jfirst, bool jlast) {
+  uint32_t l = __shfl_up_sync(0xFFFFFFFFu, v, 1, 16);
+  uint32_t r = __shfl_down_sync(0xFFFFFFFFu, v, 1, 16);
+  if (jfirst) l = 0u;
+  if (jlast) r = 0u;
+  return EdgeRow{v, __funnelshift_l(l, v, 1), __funnelshift_r(v, r, 1)};
+}
+
 // Rounds at one level until a round changes nothing.  False on the cap.
 // ab_prev / be_prev: the rows across the warp boundary as last seen.
-template <int CONN, bool thin>
+template <int CONN>
 __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint32_t& ab_prev,
                           uint32_t& be_prev) {
   const int lane = threadIdx.x & 31;
+  const bool jfirst = k.j == 0, jlast = k.j == kRegW - 1;
+  uint32_t pack = edge_pack(S);
   for (int round = 0;; ++round) {
     if (round >= k.g.cap) return false;
-    ++k.g.n_rounds;
-    k.g.n_passes += 4;
+    if (threadIdx.x == 0) {
+      s_reg_stats[STAT_ROUNDS] += 1;
+      s_reg_stats[STAT_PASSES] += 4;
+    }
     // even rows: row above the strip = last row of the strip above
     uint32_t ab = __shfl_sync(0xFFFFFFFFu, S[kRegR - 1], lane ^ 16);
     if (k.half == 0) ab = k.warp > 0 ? k.bot[(k.warp - 1) * kRegW + k.j] : 0u;
     if (__any_sync(0xFFFFFFFFu, ab != ab_prev)) need |= 1u;
     ab_prev = ab;
-    k.g.n_tests += 2 * __popc(need & 0x5555u);
-    uint32_t ch = reg_half<CONN, 0, thin>(k, S, ab, 0u, need);
+    if (lane == 0) atomicAdd(&s_reg_stats[STAT_WORD_TESTS], 64u * __popc(need & 0x5555u));
+    uint32_t Wb = __shfl_up_sync(0xFFFFFFFFu, pack, 1, 16);
+    uint32_t Eb = __shfl_down_sync(0xFFFFFFFFu, pack, 1, 16);
+    if (jfirst) Wb = 0u;
+    if (jlast) Eb = 0u;
+    uint32_t ch = reg_half<CONN, 0>(k, S, pack, Wb, Eb, edge_row(ab, jfirst, jlast), need);
     if (k.half == 0) k.top[k.warp * kRegW + k.j] = S[0];
     __syncthreads();
     // odd rows: row below the strip = first row of the strip below
@@ -164,8 +261,12 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint3
       be = (k.warp + 1) < (int)(blockDim.x >> 5) ? k.top[(k.warp + 1) * kRegW + k.j] : 0u;
     if (__any_sync(0xFFFFFFFFu, be != be_prev)) need |= 0x8000u;
     be_prev = be;
-    k.g.n_tests += 2 * __popc(need & 0xAAAAu);
-    ch |= reg_half<CONN, 1, thin>(k, S, 0u, be, need);
+    if (lane == 0) atomicAdd(&s_reg_stats[STAT_WORD_TESTS], 64u * __popc(need & 0xAAAAu));
+    Wb = __shfl_up_sync(0xFFFFFFFFu, pack, 1, 16);
+    Eb = __shfl_down_sync(0xFFFFFFFFu, pack, 1, 16);
+    if (jfirst) Wb = 0u;
+    if (jlast) Eb = 0u;
+    ch |= reg_half<CONN, 1>(k, S, pack, Wb, Eb, edge_row(be, jfirst, jlast), need);
     if (k.half == 1) k.bot[k.warp * kRegW + k.j] = S[kRegR - 1];
     if (!__syncthreads_or(ch != 0u)) return true;
   }
@@ -218,6 +319,7 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r,
   for (int li = 0; li < nlev; ++li) {
     const int o0 = c_lv.start[li], o1 = c_lv.start[li + 1];
     uint32_t newrows = 0;
+    unsigned ring = 0;  // shifted feature words read (work counter)
 #pragma unroll
     for (int g4 = 0; g4 < kRegR; g4 += 4) {
       if (!((pendrows >> g4) & 0xFu)) continue;
@@ -248,7 +350,7 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r,
             acc[u] = thin ? (acc[u] & v) : (acc[u] | v);
           }
         }
-        ++g.n_ring;
+        ++ring;
         if (((o - o0) & 3) == 3) {
           uint32_t left = 0;
 #pragma unroll
@@ -269,9 +371,11 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r,
       }
     }
     need |= __reduce_or_sync(0xFFFFFFFFu, newrows);
+    ring = __reduce_add_sync(0xFFFFFFFFu, ring);
+    if (lane == 0) atomicAdd(&s_reg_stats[STAT_RING_EVALS], ring);
     if (!__syncthreads_or(newrows != 0u)) continue;
-    ++g.n_levels;
-    if (!reg_level<CONN, thin>(k, S, need, ab_prev, be_prev)) return false;
+    if (threadIdx.x == 0) s_reg_stats[STAT_LEVELS] += 1;
+    if (!reg_level<CONN>(k, S, need, ab_prev, be_prev)) return false;
   }
   return true;
 }
@@ -454,20 +558,10 @@ __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
   }
   job_done(jb, 1);
   if (jb.stats) {
-    unsigned long long t = g.n_tests, rr = g.n_ring;
-    for (int o = 16; o > 0; o >>= 1) {
-      t += __shfl_down_sync(0xFFFFFFFFu, t, o);
-      rr += __shfl_down_sync(0xFFFFFFFFu, rr, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(jb.stats + STAT_WORD_TESTS, t);
-      atomicAdd(jb.stats + STAT_RING_EVALS, rr);
-    }
-    if (threadIdx.x == 0) {
-      atomicAdd(jb.stats + STAT_PASSES, (unsigned long long)g.n_passes);
-      atomicAdd(jb.stats + STAT_LEVELS, (unsigned long long)g.n_levels);
-      atomicAdd(jb.stats + STAT_ROUNDS, (unsigned long long)g.n_rounds);
-    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 0; i < STAT_COUNT; ++i)
+        atomicAdd(jb.stats + i, (unsigned long long)s_reg_stats[i]);
   }
 }
 
