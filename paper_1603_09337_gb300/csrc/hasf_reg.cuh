@@ -6,16 +6,18 @@
 // thread (warp w, lane l) owns word column j = l & 15 of a 16-row strip:
 // lanes 0-15 hold rows [32 w, 32 w + 16), lanes 16-31 the 16 rows below, so a
 // CTA of 512 threads covers 512 rows.  A 3 x 3 neighbourhood then comes from
-// the thread's own registers (rows above and below), warp shuffles (the words
-// left and right, and the row across the boundary of the two strips of a
-// warp), and a small shared-memory exchange of each warp's first and last row.
+// the thread's own registers (rows above and below), the bit next to the word
+// in the words left and right (exchanged as one pack of 16 rows' edge bits per
+// half-round), a warp shuffle for the row across the boundary of the two
+// strips of a warp, and a small shared-memory exchange of each warp's first
+// and last row.
 //
-// A subfield pass tests the words of its rows (8 per thread) from registers
-// and shuffles.  The two subfields of one row parity, (0, sy) and (1, sy),
-// read only rows of the other parity across rows, and words of their own row
-// through shuffles, so they run back to back without a CTA barrier (fused row
-// by row, see reg_half): a round takes two barriers (after the even rows,
-// after the odd rows), the second one OR-reducing the round's change flag.
+// A subfield pass tests the words of its rows (8 per thread) from registers.
+// The two subfields of one row parity, (0, sy) and (1, sy), read only rows of
+// the other parity across rows, so they run back to back without a CTA
+// barrier (fused row by row, see reg_half): a round takes two barriers (after
+// the even rows, after the odd rows), the second one OR-reducing the round's
+// change flag.
 //
 // The operator's priority map (snapshot F) stays a padded plane in shared
 // memory, read by the level updates exactly as in the generic kernel; the
@@ -101,7 +103,9 @@ struct EdgeRow {
 // parity SY (compile-time).  They are fused row by row: within these two
 // passes a row of parity SY reads only itself and the rows of the other
 // parity (which do not change), so finishing (0, SY) and (1, SY) on one row
-// before the next gives the same result as two full passes.
+// before the next gives the same result as two full passes.  Four rows of the
+// parity (r, r + 2, r + 4, r + 6) are tested together: their work is
+// independent, which gives each thread four chains of instructions in flight.
 //
 // Neighbour planes.  A pixel's west neighbour plane is the row shifted left by
 // one with bit 31 of the word to the left coming in at bit 0; the east plane is
@@ -109,13 +113,13 @@ struct EdgeRow {
 // 31.  Those cross-word bits come from the packs Wb (bit q = bit 31 of the
 // left neighbour's row q) and Eb (bit 16 + q = bit 0 of the right neighbour's
 // row q), exchanged once per half.  The rows of the other parity do not change
-// in the half, so the planes of row r + 1 (south) serve again as the north of
-// row r + 2.  An even pixel's cross-word neighbours all lie in the left word
-// (bit 31: an odd pixel, unchanged by the first pass); an odd pixel's in the
-// right word (bit 0: an even pixel).  So the second test needs one fresh bit,
-// the right word's updated bit 0 of the row: one shuffle, taken only when the
-// first pass changed a pixel of the row somewhere in the warp (else the first
-// test's result holds for the odd pixels too).
+// in the half: the planes of the five rows around a group of four are made
+// once.  An even pixel's cross-word neighbours all lie in the left word (bit
+// 31: an odd pixel, unchanged by the first pass); an odd pixel's in the right
+// word (bit 0: an even pixel).  So the second test needs one fresh bit per
+// row, the right word's updated bit 0: one shuffle of the four rows' bits,
+// taken only when the first pass changed a pixel of the group somewhere in
+// the warp (else the first test's result holds for the odd pixels too).
 //
 // `need` (warp-uniform, bit q = row q of either strip of the warp) says which
 // rows can change at all.  A row whose last test left it stable stays stable
@@ -123,80 +127,93 @@ struct EdgeRow {
 // no remaining candidate of the row is simple, except that odd-column changes
 // can re-enable even-column candidates of the same row -- then the row stays
 // marked.  A change in row r marks rows r - 1 and r + 1 (the strips of a warp
-// are stacked, so row 15 and row 0 are neighbours across them).  `pack` (bits
-// q and 16 + q: bits 31 and 0 of row q) follows the changes.  Returns the OR
-// of the changed bits.
+// are stacked, so row 15 and row 0 are neighbours across them).  Marks are
+// kept per group of four rows (a superset of the rows that changed; testing a
+// stable row changes nothing).  `pack` (bits q and 16 + q: bits 31 and 0 of
+// row q) is rebuilt for this parity's rows at the end.  Returns the OR of the
+// changed bits.
 template <int CONN, int SY>
 __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& pack,
                                              uint32_t Wb, uint32_t Eb, const EdgeRow& xr,
                                              uint32_t& need) {
   uint32_t* cr = k.cand + k.s0 * kRegPitch + k.j;
-  const bool jlast = k.j == kRegW - 1;
+  const uint32_t emask = k.j == kRegW - 1 ? 0u : 0xFFFFFFFFu;
   uint32_t changed = 0;
-  uint32_t rowchg = 0;  // rows of parity SY that changed (made warp-uniform below)
-  uint32_t again = 0;   // rows to re-test (odd-column change)
-  uint32_t n = 0, nL = 0, nR = 0;
-  bool nvalid = false;
-  if (SY == 0) {
-    n = xr.v;
-    nL = xr.l;
-    nR = xr.r;
-    nvalid = true;
-  }
+  uint32_t rowchg = 0;
+  uint32_t again = 0;
 #pragma unroll
-  for (int r = SY; r < kRegR; r += 2) {
-    if (!((need >> r) & 1u)) {
-      nvalid = false;
-      continue;
+  for (int r = SY; r < kRegR; r += 8) {
+    if (!((need >> r) & 0x55u)) continue;   // rows r, r + 2, r + 4, r + 6, tested together
+    uint32_t v[5], L[5], R[5];               // rows r - 1, r + 1, r + 3, r + 5, r + 7
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const int q = r - 1 + 2 * i;
+      if (q < 0) {
+        v[i] = xr.v; L[i] = xr.l; R[i] = xr.r;
+      } else if (q >= kRegR) {
+        v[i] = xr.v; L[i] = xr.l; R[i] = xr.r;
+      } else {
+        v[i] = S[q];
+        L[i] = __funnelshift_l(Wb << (31 - q), v[i], 1);
+        R[i] = __funnelshift_r(v[i], Eb >> (16 + q), 1);
+      }
     }
-    if (!nvalid && r > 0) {  // row r - 1 of the strip
-      n = S[r - 1];
-      nL = __funnelshift_l(Wb << (32 - r), n, 1);
-      nR = __funnelshift_r(n, Eb >> (15 + r), 1);
+    uint32_t c[4], cw[4], wl[4], res[4], c0[4];
+    uint32_t any = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = r + 2 * i;
+      c[i] = S[q];
+      cw[i] = cr[q * kRegPitch];
+      wl[i] = Wb << (31 - q);
+      res[i] = simple_planes<CONN>(__funnelshift_r(c[i], Eb >> (16 + q), 1), R[i], v[i], L[i],
+                                   __funnelshift_l(wl[i], c[i], 1), L[i + 1], v[i + 1], R[i + 1]);
+      c0[i] = res[i] & cw[i] & 0x55555555u;
+      any |= c0[i];
     }
-    uint32_t s, sL, sR;
-    if (r + 1 < kRegR) {
-      s = S[r + 1];
-      sL = __funnelshift_l(Wb << (30 - r), s, 1);
-      sR = __funnelshift_r(s, Eb >> (17 + r), 1);
-    } else {
-      s = xr.v;
-      sL = xr.l;
-      sR = xr.r;
+    if (__any_sync(0xFFFFFFFFu, any != 0u)) {
+      uint32_t eb = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        c[i] ^= c0[i];
+        eb |= (c[i] & 1u) << i;
+      }
+      const uint32_t e = __shfl_down_sync(0xFFFFFFFFu, eb, 1, 16) & emask;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        res[i] = simple_planes<CONN>(__funnelshift_r(c[i], e >> i, 1), R[i], v[i], L[i],
+                                     __funnelshift_l(wl[i], c[i], 1), L[i + 1], v[i + 1],
+                                     R[i + 1]);
+      rowchg |= 0x55u << r;
     }
-    uint32_t c = S[r];
-    const uint32_t cw = cr[r * kRegPitch];
-    const uint32_t wl = Wb << (31 - r);
-    uint32_t res = simple_planes<CONN>(__funnelshift_r(c, Eb >> (16 + r), 1), nR, n, nL,
-                                       __funnelshift_l(wl, c, 1), sL, s, sR);
-    const uint32_t chg0 = res & cw & 0x55555555u;
-    if (__any_sync(0xFFFFFFFFu, chg0 != 0u)) {
-      c ^= chg0;  // candidates lie in S for a thinning, outside it for a thickening
-      uint32_t e = __shfl_down_sync(0xFFFFFFFFu, c, 1, 16);
-      if (jlast) e = 0u;
-      res = simple_planes<CONN>(__funnelshift_r(c, e, 1), nR, n, nL, __funnelshift_l(wl, c, 1),
-                                sL, s, sR);
-      rowchg |= 1u << r;
+    uint32_t any1 = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = r + 2 * i;
+      const uint32_t c1 = res[i] & cw[i] & 0xAAAAAAAAu;
+      const uint32_t ch = c0[i] | c1;
+      S[q] = c[i] ^ c1;
+      if (ch) cr[q * kRegPitch] = cw[i] ^ ch;
+      changed |= ch;
+      any1 |= c1;
     }
-    const uint32_t chg1 = res & cw & 0xAAAAAAAAu;
-    const uint32_t chg = chg0 | chg1;
-    if (chg) {
-      S[r] = c ^ chg1;
-      cr[r * kRegPitch] = cw ^ chg;
-      changed |= chg;
-      pack ^= ((chg0 << (16 + r)) & (1u << (16 + r))) | ((chg1 >> (31 - r)) & (1u << r));
+    if (__any_sync(0xFFFFFFFFu, any1 != 0u)) {
+      rowchg |= 0x55u << r;
+      again |= 0x55u << r;
     }
-    if (chg1) {
-      rowchg |= 1u << r;
-      again |= 1u << r;
-    }
-    n = s;
-    nL = sL;
-    nR = sR;
-    nvalid = true;
   }
-  rowchg = __reduce_or_sync(0xFFFFFFFFu, rowchg);
-  again = __reduce_or_sync(0xFFFFFFFFu, again);
+  // bits 31 and 0 of this parity's rows, rebuilt into the pack
+  {
+    uint32_t hb = 0, lb = 0;
+#pragma unroll
+    for (int q = kRegR - 2 + SY; q >= 0; q -= 2) hb = __funnelshift_l(S[q], hb, 2);
+#pragma unroll
+    for (int q = SY; q < kRegR; q += 2) lb = __funnelshift_r(lb, S[q], 2);
+    if (SY == 0) hb >>= 1;
+    else lb <<= 1;
+    const uint32_t keep = SY ? 0x55555555u : 0xAAAAAAAAu;
+    pack = (pack & keep) | (hb & ~keep & 0xFFFFu) | (lb & ~keep & 0xFFFF0000u);
+  }
   // rows of this parity were tested: keep only those an odd-column change
   // may have re-enabled, then mark the neighbours of the changed rows
   need &= ~(SY ? 0xAAAAu : 0x5555u);
