@@ -179,7 +179,21 @@ int hasf_drain(hasf_ctx *ctx);
  *   HASF_OPT_HOST_MAPPED (0/1): hasf_smooth_host moves page-locked,
  *                        device-mapped caller buffers with one launch of the
  *                        library's copy kernel per direction (1, default)
- *                        instead of one copy call per buffer (0).
+ *                        instead of one copy call per buffer (0);
+ *   HASF_OPT_WAIT_DEADLINE_MS (0..60000): how long a CTA of a gang waits at
+ *                        the gang barrier for the others before the job gives
+ *                        up with HASF_ETIMEOUT, 0 = 4000 ms;
+ *   HASF_OPT_FAULT_GANG_SKIP (>= 0): fault injection for tests of the failure
+ *                        path -- k >= 1 makes CTA 0 of every gang of two or
+ *                        more CTAs leave its job at its k-th barrier without
+ *                        arriving, as a CTA that died would; the others' waits
+ *                        run out at the deadline and the job reports
+ *                        HASF_ETIMEOUT (no device fault; the context stays
+ *                        usable); 0 = off;
+ *   HASF_OPT_FAULT_ALLOC (>= 0): fault injection -- the n-th device or pinned
+ *                        host allocation the context makes from now on fails
+ *                        as if the memory were exhausted (the call returns
+ *                        HASF_ENOMEM); 0 = off.
  * Errors: HASF_EINVAL for an unknown option or value. */
 enum {
     HASF_OPT_FORCE_GANG = 1,
@@ -190,7 +204,10 @@ enum {
     HASF_OPT_STATS = 6,
     HASF_OPT_GENERIC_ONLY = 7,
     HASF_OPT_TILES = 8,
-    HASF_OPT_HOST_MAPPED = 9
+    HASF_OPT_HOST_MAPPED = 9,
+    HASF_OPT_WAIT_DEADLINE_MS = 10,
+    HASF_OPT_FAULT_GANG_SKIP = 11,
+    HASF_OPT_FAULT_ALLOC = 12
 };
 int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
 

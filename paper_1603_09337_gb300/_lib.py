@@ -23,6 +23,9 @@ OPT_STATS = 6
 OPT_GENERIC_ONLY = 7
 OPT_TILES = 8
 OPT_HOST_MAPPED = 9
+OPT_WAIT_DEADLINE_MS = 10
+OPT_FAULT_GANG_SKIP = 11
+OPT_FAULT_ALLOC = 12
 STAT_NAMES = ("word_tests", "ring_evals", "passes", "levels", "rounds", "launches")
 
 OP_THIN, OP_THICK, OP_HC, OP_HF = 1, 2, 3, 4

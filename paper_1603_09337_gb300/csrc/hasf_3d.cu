@@ -349,7 +349,7 @@ hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
   v.gtid = m.y * blockDim.x + threadIdx.x;
   v.gthreads = jb.gang * blockDim.x;
   v.solo = jb.gang == 1;
-  v.gm.init(jb.sync, jb.gang, &flag);
+  v.gm.init(jb.sync, jb.gang, &flag, jb.deadline_ms, jb.fault_skip, m.y);
   const int rem = jb.w & 31;
   v.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
   v.n_tests = v.n_ring = v.n_rounds = v.n_levels = 0;

@@ -85,6 +85,8 @@ struct Options {
   int stats = 0;
   int generic_only = 0;
   int host_mapped = 1;  // hasf_smooth_host: mapped pinned buffers used in place
+  int wait_deadline_ms = 0;  // gang barrier wait limit, 0 = 4000 ms
+  int fault_gang_skip = 0;   // fault injection: CTA 0 of a gang stops at its k-th barrier
 };
 
 struct Batch {  // one server launch in flight
@@ -143,6 +145,10 @@ struct hasf_ctx {
   std::thread worker;
   bool worker_running = false;
 
+  // fault injection: the n-th device or pinned-host allocation from now fails
+  // (0 = off); counted down by every allocation of the context
+  std::atomic<long long> fault_alloc{0};
+
   // autotuner: size bucket -> CTAs per image (0 = one-CTA generic kernel)
   std::map<std::tuple<int, int, int>, int> tune;
 };
@@ -161,6 +167,29 @@ int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return HASF_OK;
   if (e == cudaErrorMemoryAllocation) return HASF_ENOMEM;
   return HASF_ECUDA;
+}
+
+// Whether the allocation about to be made is the injected failure.
+bool alloc_fault(hasf_ctx* ctx) {
+  long long n = ctx->fault_alloc.load();
+  while (n > 0 && !ctx->fault_alloc.compare_exchange_weak(n, n - 1)) {
+  }
+  return n == 1;
+}
+
+// cudaMalloc / cudaMallocAsync / cudaHostAlloc of the context, through the
+// allocation fault injection.
+cudaError_t ctx_malloc(hasf_ctx* ctx, void** p, size_t bytes) {
+  if (alloc_fault(ctx)) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+cudaError_t ctx_malloc_async(hasf_ctx* ctx, void** p, size_t bytes, cudaStream_t s) {
+  if (alloc_fault(ctx)) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, s);
+}
+cudaError_t ctx_host_alloc(hasf_ctx* ctx, void** p, size_t bytes, unsigned flags) {
+  if (alloc_fault(ctx)) return cudaErrorMemoryAllocation;
+  return cudaHostAlloc(p, bytes, flags);
 }
 
 int ceil_log2(int v) {
@@ -276,6 +305,8 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
     const long long px = (long long)im.width * im.height;
     j.cap = ctx->opt.round_cap > 0 ? (int)std::min<long long>(ctx->opt.round_cap, INT_MAX)
                                    : (int)std::min<long long>(px + 2, INT_MAX);
+    j.deadline_ms = ctx->opt.wait_deadline_ms;
+    j.fault_skip = ctx->opt.fault_gang_skip;
     const size_t gwords = (size_t)im.height * j.wpr;
     j.g0 = base ? (uint32_t*)(base + off) : nullptr;
     off += align_up(gwords * 4);
@@ -488,6 +519,7 @@ int ensure_arena(hasf_ctx* ctx, size_t bytes, cudaStream_t s) {
     ctx->arena = nullptr;
     ctx->arena_bytes = 0;
   }
+  if (alloc_fault(ctx)) return HASF_ENOMEM;
   size_t want = std::min(ctx->budget, std::max(bytes, bytes + bytes / 4));
   cudaError_t e = cudaMalloc(&ctx->arena, want);
   if (e != cudaSuccess) {
@@ -619,8 +651,9 @@ bool launch_next(hasf_ctx* ctx) {  // ctx->mu held
   Plan p;
   const int n = (int)imgs.size();
   b.bytes = build_plan(ctx, imgs.data(), n, OP_HASF, p, nullptr, nullptr);
-  cudaError_t e = cudaMallocAsync(&b.mem, b.bytes, b.stream);
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&b.h_status, sizeof(int) * n, cudaHostAllocMapped);
+  cudaError_t e = ctx_malloc_async(ctx, &b.mem, b.bytes, b.stream);
+  if (e == cudaSuccess)
+    e = ctx_host_alloc(ctx, (void**)&b.h_status, sizeof(int) * n, cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
   int* d_notify = nullptr;
   if (e == cudaSuccess) {
@@ -811,6 +844,18 @@ int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
       if (value != 0 && value != 1) return HASF_EINVAL;
       ctx->opt.host_mapped = (int)value;
       return HASF_OK;
+    case HASF_OPT_WAIT_DEADLINE_MS:
+      if (value < 0 || value > 60000) return HASF_EINVAL;
+      ctx->opt.wait_deadline_ms = (int)value;
+      return HASF_OK;
+    case HASF_OPT_FAULT_GANG_SKIP:
+      if (value < 0 || value > INT_MAX) return HASF_EINVAL;
+      ctx->opt.fault_gang_skip = (int)value;
+      return HASF_OK;
+    case HASF_OPT_FAULT_ALLOC:
+      if (value < 0) return HASF_EINVAL;
+      ctx->fault_alloc.store(value);
+      return HASF_OK;
     default:
       return HASF_EINVAL;
   }
@@ -907,6 +952,8 @@ int hasf_smooth3d(hasf_ctx* ctx, const hasf_volume* vols, int n, void* stream) {
       j.gang = volume_gang(ctx, v, n);
       const long long vox = (long long)v.width * v.height * v.depth;
       j.cap = ctx->opt.round_cap > 0 ? ctx->opt.round_cap : (int)std::min<long long>(vox + 2, INT_MAX);
+      j.deadline_ms = ctx->opt.wait_deadline_ms;
+      j.fault_skip = ctx->opt.fault_gang_skip;
       const size_t pb = align_up((size_t)v.depth * v.height * j.wpr * 4);
       uint32_t** planes[7] = {&j.S, &j.F, &j.cand, &j.M, &j.g0, &j.cp, &j.dp};
       for (int q = 0; q < 7; ++q) {
@@ -1029,7 +1076,7 @@ int smooth_host_mapped(hasf_ctx* ctx, const hasf_image* maps, int n) {
       if (ctx->io) cudaFree(ctx->io);
       ctx->io = nullptr;
       ctx->io_bytes = 0;
-      if (cudaMalloc(&ctx->io, need) != cudaSuccess) {
+      if (ctx_malloc(ctx, &ctx->io, need) != cudaSuccess) {
         cudaGetLastError();
         return HASF_ENOMEM;
       }
@@ -1130,7 +1177,7 @@ int smooth_host_staged(hasf_ctx* ctx, const hasf_image* imgs, int n) {
       if (ctx->io) cudaFree(ctx->io);
       ctx->io = nullptr;
       ctx->io_bytes = 0;
-      e = cudaMalloc(&ctx->io, io);
+      e = ctx_malloc(ctx, &ctx->io, io);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return HASF_ENOMEM;
@@ -1149,7 +1196,7 @@ int smooth_host_staged(hasf_ctx* ctx, const hasf_image* imgs, int n) {
       if (ctx->pinned) cudaFreeHost(ctx->pinned);
       ctx->pinned = nullptr;
       ctx->pinned_bytes = 0;
-      e = cudaHostAlloc(&ctx->pinned, io, 0);
+      e = ctx_host_alloc(ctx, &ctx->pinned, io, 0);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return HASF_ENOMEM;
@@ -1293,7 +1340,7 @@ int hasf_graph_create(hasf_ctx* ctx, const hasf_image* imgs, int n, hasf_graph**
     delete g;
     return HASF_EBUDGET;
   }
-  cudaError_t e = cudaMalloc(&g->mem, g->bytes);
+  cudaError_t e = ctx_malloc(ctx, &g->mem, g->bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete g;

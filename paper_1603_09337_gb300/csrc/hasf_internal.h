@@ -60,6 +60,8 @@ struct Job {
   int cap;           // rounds allowed per level before DEV_TIMEOUT
   int plane_words;   // words per padded plane (see plane_words())
   int stable;        // 1: stop after the first step r that changes nothing
+  int deadline_ms;   // gang barrier wait limit (0 = 4000 ms)
+  int fault_skip;    // fault injection: k >= 1 makes CTA 0 of a gang stop at its k-th barrier
 };
 
 // One volume job of the 3D filter.  Planes: d * h rows of wpr words, bit b of
@@ -83,6 +85,8 @@ struct Job3 {
   int rmax;
   int gang;            // CTAs of the gang
   int cap;             // rounds allowed per level
+  int deadline_ms;     // gang barrier wait limit (0 = 4000 ms)
+  int fault_skip;      // fault injection, as in Job
   int pad_;
 };
 

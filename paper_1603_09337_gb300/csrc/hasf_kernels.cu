@@ -39,7 +39,7 @@ hasf_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) 
   const int2 m = ctamap[blockIdx.x];
   const Job& jb = jobs[m.x];
   Ctx<GangMode> k;
-  k.m.init(jb.sync, jb.gang, &flag);
+  k.m.init(jb.sync, jb.gang, &flag, jb.deadline_ms, jb.fault_skip, m.y);
   init_ctx(k, jb, jb.planes, m.y * blockDim.x + threadIdx.x, jb.gang * blockDim.x);
   if (jb.conn == 4) run_job<GangMode, 4>(k, jb, jb.planes);
   else run_job<GangMode, 8>(k, jb, jb.planes);

@@ -56,7 +56,7 @@ hasf_tile_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ cta
   TileCtx<GangX> k;
   tile_init(k, jb, smem, m.y % ntx, m.y / ntx);
   k.x.gbase = jb.planes;
-  k.x.gm.init(jb.sync, jb.gang, &flag);
+  k.x.gm.init(jb.sync, jb.gang, &flag, jb.deadline_ms, jb.fault_skip, m.y);
   for (int t = threadIdx.x; t < kTileSmemWords; t += blockDim.x) smem[t] = 0u;
   __syncthreads();
   if (jb.conn == 4) tile_job<4>(k, jb, smem);
