@@ -89,12 +89,23 @@ struct Options {
   int fault_gang_skip = 0;   // fault injection: CTA 0 of a gang stops at its k-th barrier
 };
 
-struct Batch {  // one server launch in flight
+// The server's launch resources, one per concurrent batch, made once and
+// reused: a stream, a completion event, completion words in pinned
+// device-mapped host memory (one per job of a batch), and device scratch that
+// grows to the largest batch the slot has run.
+struct ServeSlot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  void* mem = nullptr;
-  size_t bytes = 0;
   int* h_status = nullptr;  // pinned and mapped, one per job: 0 running, 1 + status done
+  int* d_notify = nullptr;  // device address of h_status
+  int status_cap = 0;
+  void* mem = nullptr;
+  size_t cap = 0;
+};
+
+struct Batch {  // one server launch in flight
+  ServeSlot slot;
+  size_t bytes = 0;
   std::vector<uint64_t> tickets;
   std::vector<char> reported;
 };
@@ -135,7 +146,8 @@ struct hasf_ctx {
   std::condition_variable cv;
   std::deque<Pending> pending;
   std::vector<Batch> inflight;
-  std::vector<cudaStream_t> free_streams;
+  std::vector<ServeSlot> free_slots;
+  size_t serve_retained = 0;  // device scratch held by the slots
   std::unordered_map<uint64_t, int> finished;
   std::unordered_set<uint64_t> launched;
   std::unordered_set<uint64_t> queued;
@@ -589,7 +601,7 @@ void retire_finished(hasf_ctx* ctx) {  // ctx->mu held
     // jobs report themselves as they finish (their CTAs write the mapped flags)
     for (size_t k = 0; k < b.tickets.size(); ++k) {
       if (b.reported[k]) continue;
-      const int f = *(volatile int*)(b.h_status + k);
+      const int f = *(volatile int*)(b.slot.h_status + k);
       if (f) {
         b.reported[k] = 1;
         const int st = f - 1;
@@ -598,22 +610,19 @@ void retire_finished(hasf_ctx* ctx) {  // ctx->mu held
         ctx->cv.notify_all();
       }
     }
-    cudaError_t q = cudaEventQuery(b.done);
+    cudaError_t q = cudaEventQuery(b.slot.done);
     if (q == cudaErrorNotReady) {
       ++i;
       continue;
     }
     for (size_t k = 0; k < b.tickets.size(); ++k) {
       if (b.reported[k]) continue;
-      const int f = *(volatile int*)(b.h_status + k);
+      const int f = *(volatile int*)(b.slot.h_status + k);
       ctx->finished[b.tickets[k]] = (q == cudaSuccess && f) ? public_status(f - 1) : HASF_ECUDA;
       ctx->launched.erase(b.tickets[k]);
     }
     if (q != cudaSuccess) cudaGetLastError();
-    cudaFreeAsync(b.mem, b.stream);
-    cudaFreeHost(b.h_status);
-    cudaEventDestroy(b.done);
-    ctx->free_streams.push_back(b.stream);
+    ctx->free_slots.push_back(b.slot);  // its resources stay for the next batch
     ctx->inflight_bytes -= b.bytes;
     ctx->inflight.erase(ctx->inflight.begin() + i);
     ctx->cv.notify_all();
@@ -624,8 +633,61 @@ void retire_finished(hasf_ctx* ctx) {  // ctx->mu held
 // batch holds jobs of one kind -- images the single-tile kernel takes, or
 // larger ones -- taken in arrival order starting from the oldest job, so that
 // short jobs never wait in a launch for a long one.
+// Give a slot room for a batch of n jobs and `bytes` of scratch.  Scratch
+// grows with a quarter of slack while the slots' total stays within the
+// budget; idle slots give theirs back when it would not.
+int slot_reserve(hasf_ctx* ctx, ServeSlot& sl, int n, size_t bytes) {  // ctx->mu held
+  if (sl.status_cap < n) {
+    if (sl.h_status) cudaFreeHost(sl.h_status);
+    sl.h_status = nullptr;
+    sl.d_notify = nullptr;
+    sl.status_cap = 0;
+    const int want = std::max(n, ctx->opt.serve_batch);
+    cudaError_t e = ctx_host_alloc(ctx, (void**)&sl.h_status, sizeof(int) * want,
+                                   cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&sl.d_notify, sl.h_status, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (sl.h_status) cudaFreeHost(sl.h_status);
+      sl.h_status = nullptr;
+      return cuda_status(e);
+    }
+    sl.status_cap = want;
+  }
+  if (sl.cap < bytes) {
+    if (sl.mem) cudaFreeAsync(sl.mem, sl.stream);
+    ctx->serve_retained -= sl.cap;
+    sl.mem = nullptr;
+    sl.cap = 0;
+    size_t want = std::max(bytes, bytes + bytes / 4);
+    if (ctx->serve_retained + want > ctx->budget) want = bytes;
+    for (ServeSlot& o : ctx->free_slots) {
+      if (ctx->serve_retained + want <= ctx->budget) break;
+      if (o.mem) {
+        cudaFreeAsync(o.mem, o.stream);
+        ctx->serve_retained -= o.cap;
+        o.mem = nullptr;
+        o.cap = 0;
+      }
+    }
+    cudaError_t e = ctx_malloc_async(ctx, &sl.mem, want, sl.stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      sl.mem = nullptr;
+      return cuda_status(e);
+    }
+    sl.cap = want;
+    ctx->serve_retained += want;
+  }
+  return HASF_OK;
+}
+
+// Admit pending jobs that fit the budget into one batch and launch it.  A
+// batch holds jobs of one kind -- images the single-tile kernel takes, or
+// larger ones -- taken in arrival order starting from the oldest job, so that
+// short jobs never wait in a launch for a long one.
 bool launch_next(hasf_ctx* ctx) {  // ctx->mu held
-  if (ctx->pending.empty() || ctx->free_streams.empty()) return false;
+  if (ctx->pending.empty() || ctx->free_slots.empty()) return false;
   std::vector<hasf_image> imgs;
   std::vector<uint64_t> tickets;
   size_t bytes = 0;
@@ -645,38 +707,30 @@ bool launch_next(hasf_ctx* ctx) {  // ctx->mu held
   }
   if (imgs.empty()) return false;
   Batch b;
-  b.stream = ctx->free_streams.back();
-  ctx->free_streams.pop_back();
+  b.slot = ctx->free_slots.back();
+  ctx->free_slots.pop_back();
   b.tickets = tickets;
   Plan p;
   const int n = (int)imgs.size();
   b.bytes = build_plan(ctx, imgs.data(), n, OP_HASF, p, nullptr, nullptr);
-  cudaError_t e = ctx_malloc_async(ctx, &b.mem, b.bytes, b.stream);
-  if (e == cudaSuccess)
-    e = ctx_host_alloc(ctx, (void**)&b.h_status, sizeof(int) * n, cudaHostAllocMapped);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
-  int* d_notify = nullptr;
-  if (e == cudaSuccess) {
-    std::memset(b.h_status, 0, sizeof(int) * n);
-    e = cudaHostGetDevicePointer((void**)&d_notify, b.h_status, 0);
-  }
   b.reported.assign(n, 0);
-  int rc = cuda_status(e);
+  int rc = slot_reserve(ctx, b.slot, n, b.bytes);
   if (rc == HASF_OK) {
-    build_plan(ctx, imgs.data(), n, OP_HASF, p, (char*)b.mem, nullptr, d_notify);
-    e = cudaMemsetAsync((char*)b.mem + p.off_status, 0, sizeof(int) * n, b.stream);
+    // the slot's last batch has finished (its event was seen complete): the
+    // words may be cleared on the host
+    std::memset(b.slot.h_status, 0, sizeof(int) * n);
+    build_plan(ctx, imgs.data(), n, OP_HASF, p, (char*)b.slot.mem, nullptr, b.slot.d_notify);
+    cudaError_t e = cudaMemsetAsync((char*)b.slot.mem + p.off_status, 0, sizeof(int) * n,
+                                    b.slot.stream);
     rc = cuda_status(e);
-    if (rc == HASF_OK) rc = launch_plan(ctx, p, (char*)b.mem, b.stream, true, false);
-    if (rc == HASF_OK) rc = cuda_status(cudaEventRecord(b.done, b.stream));
+    if (rc == HASF_OK) rc = launch_plan(ctx, p, (char*)b.slot.mem, b.slot.stream, true, false);
+    if (rc == HASF_OK) rc = cuda_status(cudaEventRecord(b.slot.done, b.slot.stream));
   }
   if (rc != HASF_OK) {
     cudaGetLastError();
-    cudaStreamSynchronize(b.stream);
+    cudaStreamSynchronize(b.slot.stream);
     for (uint64_t t : tickets) ctx->finished[t] = rc;
-    if (b.mem) cudaFreeAsync(b.mem, b.stream);
-    if (b.h_status) cudaFreeHost(b.h_status);
-    if (b.done) cudaEventDestroy(b.done);
-    ctx->free_streams.push_back(b.stream);
+    ctx->free_slots.push_back(b.slot);
     ctx->cv.notify_all();
     return true;
   }
@@ -709,10 +763,14 @@ void worker_main(hasf_ctx* ctx) {
 int start_server(hasf_ctx* ctx) {  // ctx->mu held
   if (ctx->worker_running) return HASF_OK;
   for (int i = 0; i < ctx->opt.serve_streams; ++i) {
-    cudaStream_t st;
-    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_status(e);
-    ctx->free_streams.push_back(st);
+    ServeSlot sl;
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      if (sl.stream) cudaStreamDestroy(sl.stream);
+      return cuda_status(e);
+    }
+    ctx->free_slots.push_back(sl);
   }
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, ctx->device) == cudaSuccess) {
@@ -790,7 +848,15 @@ int hasf_destroy(hasf_ctx* ctx) {
     ctx->cv.notify_all();
   }
   if (ctx->worker_running) ctx->worker.join();
-  for (cudaStream_t st : ctx->free_streams) cudaStreamDestroy(st);
+  for (ServeSlot& sl : ctx->free_slots) {
+    cudaStreamSynchronize(sl.stream);
+    if (sl.mem) cudaFreeAsync(sl.mem, sl.stream);
+    cudaStreamSynchronize(sl.stream);
+    if (sl.h_status) cudaFreeHost(sl.h_status);
+    cudaEventDestroy(sl.done);
+    cudaStreamDestroy(sl.stream);
+  }
+  ctx->free_slots.clear();
   for (cudaStream_t st : ctx->lanes) cudaStreamDestroy(st);
   cudaDeviceSynchronize();
   if (ctx->arena) cudaFree(ctx->arena);
