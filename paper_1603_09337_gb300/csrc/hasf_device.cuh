@@ -216,6 +216,15 @@ __device__ __forceinline__ void walk_init(Walk& wk, int step, int L, int g, int 
   wk.dm = nwarps % wk.delta;
 }
 
+// Three-input logic as one instruction: LUT is the truth table evaluated on
+// a = 0xF0, b = 0xCC, c = 0xAA.
+template <unsigned LUT>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
+
 // Simple-point test of the 32 pixels of the word `c` given the 3 x 3 words
 // around it.  Bit b of the result is 1 iff pixel b is simple (removable when
 // in the set, addable when not).
@@ -239,9 +248,8 @@ __device__ __forceinline__ uint32_t simple_bits(uint32_t nw, uint32_t n, uint32_
   const uint32_t b = ~x2 & (x3 | x4);
   const uint32_t cc = ~x4 & (x5 | x6);
   const uint32_t d = ~x6 & (x7 | x0);
-  const uint32_t odd = a ^ b ^ cc ^ d;
-  const uint32_t two = (a & b) | (cc & d) | ((a | b) & (cc | d));
-  return odd & ~two;
+  // exactly one of the four terms: d ? none of a, b, cc : exactly one of a, b, cc
+  return lop3<0x3Au>(d, lop3<0xFEu>(a, b, cc), lop3<0x16u>(a, b, cc));
 }
 
 // Word whose bit b is G(32 j + b + dx, y2), where G = F xor inv inside the

@@ -67,21 +67,14 @@ struct RegCtx {
   bool jin;             // j < words per row of the image
 };
 
-// Three-input logic as one instruction: LUT is the truth table evaluated on
-// a = 0xF0, b = 0xCC, c = 0xAA.
-template <unsigned LUT>
-__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
-  return d;
-}
-
 // Simple-point test of 32 pixels from their eight neighbour planes (bit b of
 // x_k = neighbour k of pixel b, in the order E, NE, N, NW, W, SW, S, SE), by
 // the crossing count of Sec. 2's T = Tbar = 1: with the four terms
 // [x_k = 0 and (x_{k+1} or x_{k+2}) = 1] for k = E, N, W, S (cyclic order),
 // exactly one of them holds.  (4,8) adjacency takes the complemented planes,
-// folded into the terms' truth table.  Nine three-input logic instructions.
+// folded into the terms' truth table.  Seven three-input logic instructions:
+// four terms, then "exactly one of four" as d ? none of a, b, c : exactly one
+// of a, b, c.
 template <int CONN>
 __device__ __forceinline__ uint32_t simple_planes(uint32_t x0, uint32_t x1, uint32_t x2,
                                                   uint32_t x3, uint32_t x4, uint32_t x5,
@@ -89,8 +82,8 @@ __device__ __forceinline__ uint32_t simple_planes(uint32_t x0, uint32_t x1, uint
   constexpr unsigned T = CONN == 8 ? 0x0Eu : 0x70u;  // ~a & (b | c), or a & ~(b & c)
   const uint32_t a = lop3<T>(x0, x1, x2), b = lop3<T>(x2, x3, x4);
   const uint32_t c = lop3<T>(x4, x5, x6), d = lop3<T>(x6, x7, x0);
-  const uint32_t u = a | b, v = c | d;
-  return lop3<0x14u>(a, b, v) | lop3<0x14u>(c, d, u);  // (a ^ b) & ~v | (c ^ d) & ~u
+  // exactly one of a, b, c, d = d ? none of a, b, c : exactly one of a, b, c
+  return lop3<0x3Au>(d, lop3<0xFEu>(a, b, c), lop3<0x16u>(a, b, c));
 }
 
 // A row next to the thread's strip (the last row of the strip above, or the
@@ -120,6 +113,8 @@ struct EdgeRow {
 // row, the right word's updated bit 0: one shuffle of the four rows' bits,
 // taken only when the first pass changed a pixel of the group somewhere in
 // the warp (else the first test's result holds for the odd pixels too).
+// The candidates are stored back unconditionally (a store costs less than
+// the test that would skip it).
 //
 // `need` (warp-uniform, bit q = row q of either strip of the warp) says which
 // rows can change at all.  A row whose last test left it stable stays stable
@@ -130,8 +125,8 @@ struct EdgeRow {
 // are stacked, so row 15 and row 0 are neighbours across them).  Marks are
 // kept per group of four rows (a superset of the rows that changed; testing a
 // stable row changes nothing).  `pack` (bits q and 16 + q: bits 31 and 0 of
-// row q) is rebuilt for this parity's rows at the end.  Returns the OR of the
-// changed bits.
+// row q) is rebuilt for this parity's rows at the end.  Returns non-zero when
+// a pixel changed.
 template <int CONN, int SY>
 __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& pack,
                                              uint32_t Wb, uint32_t Eb, const EdgeRow& xr,
@@ -172,34 +167,32 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], ui
       any |= c0[i];
     }
     if (__any_sync(0xFFFFFFFFu, any != 0u)) {
-      uint32_t eb = 0;
+      // odd pixels: the right word's bit 0 after its even-column pass, one
+      // shuffle per row
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         c[i] ^= c0[i];
-        eb |= (c[i] & 1u) << i;
-      }
-      const uint32_t e = __shfl_down_sync(0xFFFFFFFFu, eb, 1, 16) & emask;
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        res[i] = simple_planes<CONN>(__funnelshift_r(c[i], e >> i, 1), R[i], v[i], L[i],
+        const uint32_t e = __shfl_down_sync(0xFFFFFFFFu, c[i], 1, 16) & emask;
+        res[i] = simple_planes<CONN>(__funnelshift_r(c[i], e, 1), R[i], v[i], L[i],
                                      __funnelshift_l(wl[i], c[i], 1), L[i + 1], v[i + 1],
                                      R[i + 1]);
+      }
       rowchg |= 0x55u << r;
+      changed = 1u;
     }
     uint32_t any1 = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int q = r + 2 * i;
       const uint32_t c1 = res[i] & cw[i] & 0xAAAAAAAAu;
-      const uint32_t ch = c0[i] | c1;
       S[q] = c[i] ^ c1;
-      if (ch) cr[q * kRegPitch] = cw[i] ^ ch;
-      changed |= ch;
+      cr[q * kRegPitch] = cw[i] ^ c0[i] ^ c1;
       any1 |= c1;
     }
     if (__any_sync(0xFFFFFFFFu, any1 != 0u)) {
       rowchg |= 0x55u << r;
       again |= 0x55u << r;
+      changed = 1u;
     }
   }
   // bits 31 and 0 of this parity's rows, rebuilt into the pack
