@@ -124,7 +124,8 @@ struct EdgeRow {
 // marked.  A change in row r marks rows r - 1 and r + 1 (the strips of a warp
 // are stacked, so row 15 and row 0 are neighbours across them).  Marks are
 // kept per group of four rows (a superset of the rows that changed; testing a
-// stable row changes nothing).  `pack` (bits q and 16 + q: bits 31 and 0 of
+// stable row changes nothing).  A group without a candidate anywhere in the
+// warp is skipped.  `pack` (bits q and 16 + q: bits 31 and 0 of
 // row q) is rebuilt for this parity's rows at the end.  Returns non-zero when
 // a pixel changed.
 template <int CONN, int SY>
@@ -139,6 +140,13 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], ui
 #pragma unroll
   for (int r = SY; r < kRegR; r += 8) {
     if (!((need >> r) & 0x55u)) continue;   // rows r, r + 2, r + 4, r + 6, tested together
+    uint32_t cw[4], anyc = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      cw[i] = cr[(r + 2 * i) * kRegPitch];
+      anyc |= cw[i];
+    }
+    if (!__any_sync(0xFFFFFFFFu, anyc != 0u)) continue;
     uint32_t v[5], L[5], R[5];               // rows r - 1, r + 1, r + 3, r + 5, r + 7
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
@@ -153,13 +161,12 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], ui
         R[i] = __funnelshift_r(v[i], Eb >> (16 + q), 1);
       }
     }
-    uint32_t c[4], cw[4], wl[4], res[4], c0[4];
+    uint32_t c[4], wl[4], res[4], c0[4];
     uint32_t any = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int q = r + 2 * i;
       c[i] = S[q];
-      cw[i] = cr[q * kRegPitch];
       wl[i] = Wb << (31 - q);
       res[i] = simple_planes<CONN>(__funnelshift_r(c[i], Eb >> (16 + q), 1), R[i], v[i], L[i],
                                    __funnelshift_l(wl[i], c[i], 1), L[i + 1], v[i + 1], R[i + 1]);
