@@ -193,7 +193,13 @@ int hasf_drain(hasf_ctx *ctx);
  *   HASF_OPT_FAULT_ALLOC (>= 0): fault injection -- the n-th device or pinned
  *                        host allocation the context makes from now on fails
  *                        as if the memory were exhausted (the call returns
- *                        HASF_ENOMEM); 0 = off.
+ *                        HASF_ENOMEM); 0 = off;
+ *   HASF_OPT_ROW_GROUP   (0, 1, 2 or 4): the single-tile register kernel's sweep
+ *                        schedule -- how many rows of one parity a thread tests
+ *                        together (sharing their neighbour rows, one warp vote
+ *                        and one shuffle round); 0 (default) = the autotuner's
+ *                        choice for the image's size bucket, else 4.  The result
+ *                        is the same for every schedule.
  * Errors: HASF_EINVAL for an unknown option or value. */
 enum {
     HASF_OPT_FORCE_GANG = 1,
@@ -207,7 +213,8 @@ enum {
     HASF_OPT_HOST_MAPPED = 9,
     HASF_OPT_WAIT_DEADLINE_MS = 10,
     HASF_OPT_FAULT_GANG_SKIP = 11,
-    HASF_OPT_FAULT_ALLOC = 12
+    HASF_OPT_FAULT_ALLOC = 12,
+    HASF_OPT_ROW_GROUP = 13
 };
 int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
 
@@ -246,12 +253,23 @@ int hasf_graph_destroy(hasf_graph *graph);
  * the image fits it, and gangs of 1, 2, 4, ... CTAs -- on a synthetic image of
  * the given size, in batches that fill the GPU (throughput, the batched use),
  * and records the fastest for the size bucket (powers of two of width and
- * height, and rmax).  Later batches use the recorded choice.  *ctas receives
- * it: -1 = tiled, 0 = one-CTA generic, g > 0 = gang of g CTAs (and 0 for
- * images the single-tile kernel takes).  Synchronous. */
+ * height, and rmax).  For images the single-tile register kernel takes it
+ * times that kernel's sweep schedules instead (1, 2 or 4 rows tested
+ * together, see HASF_OPT_ROW_GROUP) and records the fastest.  Later batches
+ * use the recorded choices.  *ctas receives the CTAs per image: -1 = tiled,
+ * 0 = one-CTA generic, g > 0 = gang of g CTAs (and 0 for images the
+ * single-tile kernel takes).  Synchronous. */
 int hasf_autotune(hasf_ctx *ctx, int32_t width, int32_t height, int32_t rmax,
                   int32_t connectivity, int32_t *ctas);
-/* Save / load the tuned choices as text ("log2w log2h rmax ctas" lines). */
+/* The choice recorded for the size bucket of (width, height, rmax): *ctas as
+ * for hasf_autotune and *rows_per_group the register kernel's sweep schedule
+ * (1, 2 or 4; 0 for images that kernel does not take).  Errors: HASF_EINVAL,
+ * HASF_ENOTFOUND (nothing recorded for the bucket). */
+int hasf_tuning_get(hasf_ctx *ctx, int32_t width, int32_t height, int32_t rmax,
+                    int32_t *ctas, int32_t *rows_per_group);
+/* Save / load the tuned choices as text ("log2w log2h rmax ctas group" lines;
+ * group 0 = a choice of CTAs per image, 1/2/4 = a register-kernel schedule;
+ * lines of four fields are read as group 0). */
 int hasf_tuning_save(hasf_ctx *ctx, const char *path);
 int hasf_tuning_load(hasf_ctx *ctx, const char *path);
 

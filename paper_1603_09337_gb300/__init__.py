@@ -209,6 +209,15 @@ class Context:
               "hasf_autotune")
         return c.value
 
+    def tuning_get(self, width: int, height: int, rmax: int):
+        """(ctas, rows_per_group) recorded for the size bucket, or None."""
+        c, g = ctypes.c_int32(), ctypes.c_int32()
+        rc = self.lib.hasf_tuning_get(self.h, width, height, rmax, ctypes.byref(c), ctypes.byref(g))
+        if rc == _lib.HASF_ENOTFOUND:
+            return None
+        check(rc, "hasf_tuning_get")
+        return c.value, g.value
+
     def tuning_save(self, path: str):
         check(self.lib.hasf_tuning_save(self.h, path.encode()), "hasf_tuning_save")
 

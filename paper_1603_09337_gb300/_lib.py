@@ -26,6 +26,7 @@ OPT_HOST_MAPPED = 9
 OPT_WAIT_DEADLINE_MS = 10
 OPT_FAULT_GANG_SKIP = 11
 OPT_FAULT_ALLOC = 12
+OPT_ROW_GROUP = 13
 STAT_NAMES = ("word_tests", "ring_evals", "passes", "levels", "rounds", "launches")
 
 OP_THIN, OP_THICK, OP_HC, OP_HF = 1, 2, 3, 4
@@ -37,7 +38,7 @@ EXPORTS = (
     "hasf_set_option", "hasf_strerror", "hasf_edt", "hasf_operator", "hasf_simple_table",
     "hasf_levels", "hasf_read_stats", "hasf_smooth_noalloc", "hasf_graph_create",
     "hasf_graph_launch", "hasf_graph_destroy", "hasf_autotune", "hasf_tuning_save",
-    "hasf_tuning_load", "hasf_smooth3d",
+    "hasf_tuning_load", "hasf_tuning_get", "hasf_smooth3d",
 )
 
 
@@ -111,6 +112,7 @@ def _declare(lib):
     lib.hasf_autotune.argtypes = [vp, i32, i32, i32, i32, ctypes.POINTER(i32)]
     lib.hasf_tuning_save.argtypes = [vp, ctypes.c_char_p]
     lib.hasf_tuning_load.argtypes = [vp, ctypes.c_char_p]
+    lib.hasf_tuning_get.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.hasf_smooth3d.argtypes = [vp, ctypes.POINTER(HasfVolume), ci, vp]
     for name in EXPORTS:
         if name != "hasf_strerror":

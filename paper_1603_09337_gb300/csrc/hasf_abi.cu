@@ -60,7 +60,9 @@ int validate(const hasf_image* im) {
 struct Plan {
   std::vector<Job> jobs;
   std::vector<int> order;       // resident jobs (generic kernel), largest work first
-  std::vector<int> reg_order;   // resident jobs (register kernel), largest work first
+  std::vector<int> reg_order;   // resident jobs (register kernel): by sweep schedule
+                                // (4, 2, 1 rows per group), then largest work first
+  int reg_split[3] = {0, 0, 0}; // jobs of each schedule, in that order
   size_t reg_smem = 0;          // dynamic shared memory of the register launch
   std::map<int, std::vector<int>> tile_groups;  // tiles per image -> cluster jobs
   std::vector<int2> tctamap;    // tiled gang CTAs (job, tile)
@@ -87,6 +89,7 @@ struct Options {
   int host_mapped = 1;  // hasf_smooth_host: mapped pinned buffers used in place
   int wait_deadline_ms = 0;  // gang barrier wait limit, 0 = 4000 ms
   int fault_gang_skip = 0;   // fault injection: CTA 0 of a gang stops at its k-th barrier
+  int row_group = 0;         // register kernel's rows per sweep group: 0 = tuned / 4, or 1, 2, 4
 };
 
 // The server's launch resources, one per concurrent batch, made once and
@@ -163,6 +166,9 @@ struct hasf_ctx {
 
   // autotuner: size bucket -> CTAs per image (0 = one-CTA generic kernel)
   std::map<std::tuple<int, int, int>, int> tune;
+  // autotuner: size bucket of the register kernel -> rows per sweep group
+  std::map<std::tuple<int, int, int>, int> tune_group;
+  std::mutex tune_mu;  // guards tune_group (read by plans built under ctx->mu and without it)
 };
 
 struct hasf_graph {
@@ -213,6 +219,16 @@ std::tuple<int, int, int> tune_key(const hasf_image& im) {
   return std::make_tuple(ceil_log2(im.width), ceil_log2(im.height), im.rmax);
 }
 
+// Rows per sweep group of a register-kernel image: forced by the option, else
+// the autotuner's choice for its size bucket, else 4.
+int reg_group(hasf_ctx* ctx, const hasf_image& im) {
+  if (ctx->opt.row_group) return ctx->opt.row_group;
+  std::lock_guard<std::mutex> lk(ctx->tune_mu);
+  auto it = ctx->tune_group.find(tune_key(im));
+  return it != ctx->tune_group.end() ? it->second : 4;
+}
+int group_slot(int g) { return g == 4 ? 0 : (g == 2 ? 1 : 2); }
+
 bool fits_resident(const hasf_ctx* ctx, const hasf_image& im) {
   // keep 1 KB of the per-block limit for the kernel's static shared memory
   return resident_smem_bytes(im.width, im.height) + 1024 <= ctx->max_smem;
@@ -262,6 +278,8 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
   p.jobs.assign(n, Job{});
   p.order.clear();
   p.reg_order.clear();
+  p.reg_split[0] = p.reg_split[1] = p.reg_split[2] = 0;
+  std::vector<int> reg_by_group[3];
   p.reg_smem = 0;
   p.tile_groups.clear();
   p.tctamap.clear();
@@ -343,7 +361,7 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
       p.gang_jobs.push_back(i);
     } else if (path[i] == 3) {
       j.gang = 1;
-      p.reg_order.push_back(i);
+      reg_by_group[group_slot(reg_group(ctx, im))].push_back(i);
       p.reg_smem = std::max(p.reg_smem, reg_kernel_smem(im.width, im.height));
     } else if (path[i] == 1) {
       j.gang = tile_count(im.width, im.height);
@@ -373,7 +391,11 @@ size_t build_plan(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, Plan& p,
     return wa > wb;
   };
   std::stable_sort(p.order.begin(), p.order.end(), by_work);
-  std::stable_sort(p.reg_order.begin(), p.reg_order.end(), by_work);
+  for (int gi = 0; gi < 3; ++gi) {
+    std::stable_sort(reg_by_group[gi].begin(), reg_by_group[gi].end(), by_work);
+    p.reg_order.insert(p.reg_order.end(), reg_by_group[gi].begin(), reg_by_group[gi].end());
+    p.reg_split[gi] = (int)reg_by_group[gi].size();
+  }
   for (auto& kv : p.tile_groups) std::stable_sort(kv.second.begin(), kv.second.end(), by_work);
   for (int gi : p.gang_jobs)
     for (int part = 0; part < p.jobs[gi].gang; ++part) p.ctamap.push_back(make_int2(gi, part));
@@ -416,7 +438,8 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
   if (e == cudaSuccess) e = cudaMemsetAsync(base + p.off_sync, 0, p.sync_bytes, s);
   if (e != cudaSuccess) return cuda_status(e);
   const Job* d_jobs = (const Job*)(base + p.off_jobs);
-  const int groups = (p.reg_order.empty() ? 0 : 1) + (p.order.empty() ? 0 : 1) +
+  const int groups = (p.reg_split[0] > 0) + (p.reg_split[1] > 0) + (p.reg_split[2] > 0) +
+                     (p.order.empty() ? 0 : 1) +
                      (int)p.tile_groups.size() + (p.tctamap.empty() ? 0 : 1) +
                      (p.ctamap.empty() ? 0 : 1);
   const int nl = (fork && groups > 1) ? std::min<int>(groups, (int)ctx->lanes.size()) : 0;
@@ -501,12 +524,13 @@ int launch_plan(hasf_ctx* ctx, Plan& p, char* base, cudaStream_t s, bool upload 
     ++ctx->launches;
     at = end;
   }
-  if (!p.reg_order.empty()) {
+  for (int gi = 0, at = 0; gi < 3; at += p.reg_split[gi], ++gi) {
+    if (!p.reg_split[gi]) continue;
     const int per_sm = std::max(1, reg_ctas_per_sm(p.reg_smem));
-    const int grid = std::min<int>((int)p.reg_order.size(), per_sm * ctx->num_sms);
-    e = launch_reg(d_jobs, (const int*)(base + p.off_order) + p.order.size(),
-                   (int)p.reg_order.size(), grid, p.reg_smem,
-                   (unsigned*)(base + p.off_counter) + 1, lane());
+    const int grid = std::min<int>(p.reg_split[gi], per_sm * ctx->num_sms);
+    e = launch_reg(gi == 0 ? 4 : (gi == 1 ? 2 : 1), d_jobs,
+                   (const int*)(base + p.off_order) + p.order.size() + at, p.reg_split[gi], grid,
+                   p.reg_smem, (unsigned*)(base + p.off_counter) + 1 + gi, lane());
     if (e != cudaSuccess) return cuda_status(e);
     ++ctx->launches;
   }
@@ -921,6 +945,10 @@ int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
     case HASF_OPT_FAULT_ALLOC:
       if (value < 0) return HASF_EINVAL;
       ctx->fault_alloc.store(value);
+      return HASF_OK;
+    case HASF_OPT_ROW_GROUP:
+      if (value != 0 && value != 1 && value != 2 && value != 4) return HASF_EINVAL;
+      ctx->opt.row_group = (int)value;
       return HASF_OK;
     default:
       return HASF_EINVAL;
@@ -1478,6 +1506,91 @@ void tune_image(std::vector<uint8_t>& img, int w, int h) {
 }
 }  // namespace
 
+namespace {
+// Time the register kernel's sweep schedules (4, 2 and 1 rows per group) on a
+// synthetic image of the bucket's size, in batches that fill the GPU, and
+// record the fastest for the bucket.
+int tune_reg_group(hasf_ctx* ctx, const hasf_image& im) {
+  std::vector<uint8_t> host;
+  tune_image(host, im.width, im.height);
+  const size_t px = (size_t)im.width * im.height;
+  const int copies = std::max(1, 2 * ctx->num_sms);
+  uint8_t* dev = nullptr;
+  if (ctx_malloc(ctx, (void**)&dev, px * 2 * copies) != cudaSuccess) {
+    cudaGetLastError();
+    return HASF_ENOMEM;
+  }
+  for (int c = 0; c < copies; ++c)
+    cudaMemcpy(dev + px * 2 * c, host.data(), px, cudaMemcpyHostToDevice);
+  std::vector<hasf_image> batch(copies, im);
+  for (int c = 0; c < copies; ++c) {
+    batch[c].in = dev + px * 2 * c;
+    batch[c].out = dev + px * 2 * c + px;
+  }
+  const Options saved = ctx->opt;
+  cudaStream_t s = ctx->host_stream;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int rc = HASF_OK, best_g = 4;
+  float best = 1e30f;
+  for (int g : {4, 2, 1}) {
+    ctx->opt = saved;
+    ctx->opt.row_group = g;
+    rc = run_images(ctx, batch.data(), copies, OP_HASF, s);  // warm-up
+    if (rc == HASF_OK) rc = hasf_status_of(ctx, s);
+    if (rc != HASF_OK) break;
+    float ms = 1e30f;
+    for (int rep = 0; rep < 2 && rc == HASF_OK; ++rep) {
+      cudaEventRecord(a, s);
+      rc = run_images(ctx, batch.data(), copies, OP_HASF, s);
+      cudaEventRecord(b, s);
+      if (rc == HASF_OK) rc = hasf_status_of(ctx, s);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, a, b);
+      ms = std::min(ms, t);
+    }
+    if (rc != HASF_OK) break;
+    if (ms < best) {
+      best = ms;
+      best_g = g;
+    }
+  }
+  ctx->opt = saved;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(dev);
+  if (rc != HASF_OK) return rc;
+  std::lock_guard<std::mutex> lk(ctx->tune_mu);
+  ctx->tune_group[tune_key(im)] = best_g;
+  return HASF_OK;
+}
+}  // namespace
+
+int hasf_tuning_get(hasf_ctx* ctx, int32_t width, int32_t height, int32_t rmax, int32_t* ctas,
+                    int32_t* rows_per_group) {
+  if (!ctx || !ctas || !rows_per_group || width < 1 || height < 1 || rmax == 0) return HASF_EINVAL;
+  hasf_image im{};
+  im.width = width;
+  im.height = height;
+  im.rmax = rmax;
+  const auto key = tune_key(im);
+  if (reg_kernel_ok(width, height, std::abs(rmax))) {
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    auto it = ctx->tune_group.find(key);
+    if (it == ctx->tune_group.end()) return HASF_ENOTFOUND;
+    *ctas = 0;
+    *rows_per_group = it->second;
+    return HASF_OK;
+  }
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  auto it = ctx->tune.find(key);
+  if (it == ctx->tune.end()) return HASF_ENOTFOUND;
+  *ctas = it->second;
+  *rows_per_group = 0;
+  return HASF_OK;
+}
+
 int hasf_autotune(hasf_ctx* ctx, int32_t width, int32_t height, int32_t rmax, int32_t conn,
                   int32_t* ctas) {
   if (!ctx || !ctas || width < 1 || height < 1 || width > 65536 || height > 65536 || rmax < 1 ||
@@ -1490,9 +1603,9 @@ int hasf_autotune(hasf_ctx* ctx, int32_t width, int32_t height, int32_t rmax, in
   im.pitch = width;
   im.rmax = rmax;
   im.connectivity = conn;
-  if (reg_kernel_ok(width, height, rmax)) {  // the register kernel: nothing to choose
+  if (reg_kernel_ok(width, height, rmax)) {  // the register kernel: time its sweep schedules
     *ctas = 0;
-    return HASF_OK;
+    return tune_reg_group(ctx, im);
   }
   std::vector<uint8_t> host;
   tune_image(host, width, height);
@@ -1573,10 +1686,18 @@ int hasf_tuning_save(hasf_ctx* ctx, const char* path) {
   if (!ctx || !path) return HASF_EINVAL;
   FILE* f = std::fopen(path, "w");
   if (!f) return HASF_EINVAL;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  for (const auto& kv : ctx->tune)
-    std::fprintf(f, "%d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
-                 std::get<2>(kv.first), kv.second);
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (const auto& kv : ctx->tune)
+      std::fprintf(f, "%d %d %d %d 0\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                   std::get<2>(kv.first), kv.second);
+  }
+  {
+    std::lock_guard<std::mutex> lk(ctx->tune_mu);
+    for (const auto& kv : ctx->tune_group)
+      std::fprintf(f, "%d %d %d 0 %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                   std::get<2>(kv.first), kv.second);
+  }
   std::fclose(f);
   return HASF_OK;
 }
@@ -1585,10 +1706,22 @@ int hasf_tuning_load(hasf_ctx* ctx, const char* path) {
   if (!ctx || !path) return HASF_EINVAL;
   FILE* f = std::fopen(path, "r");
   if (!f) return HASF_EINVAL;
-  int a, b, c, d;
-  std::lock_guard<std::mutex> lk(ctx->mu);
-  while (std::fscanf(f, "%d %d %d %d", &a, &b, &c, &d) == 4)
-    if (a >= 0 && b >= 0 && c >= 1 && c <= kMaxR && d >= 0) ctx->tune[std::make_tuple(a, b, c)] = d;
+  // lines "log2w log2h rmax ctas [rows_per_group]"; a group of 0 or none is a
+  // choice of CTAs per image, else a register-kernel schedule
+  char line[256];
+  while (std::fgets(line, sizeof line, f)) {
+    int a, b, c, d, g = 0;
+    const int n = std::sscanf(line, "%d %d %d %d %d", &a, &b, &c, &d, &g);
+    if (n < 4 || a < 0 || b < 0 || c == 0 || c > kMaxR || c < -kMaxR) continue;
+    const auto key = std::make_tuple(a, b, c);
+    if (g == 1 || g == 2 || g == 4) {
+      std::lock_guard<std::mutex> lk(ctx->tune_mu);
+      ctx->tune_group[key] = g;
+    } else if (g == 0 && d >= -1) {
+      std::lock_guard<std::mutex> lk(ctx->mu);
+      ctx->tune[key] = d;
+    }
+  }
   std::fclose(f);
   return HASF_OK;
 }

@@ -124,8 +124,15 @@ cudaError_t launch_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cuda
 size_t reg_kernel_smem(int w, int h);
 bool reg_kernel_ok(int w, int h, int rmax);
 int reg_ctas_per_sm(size_t smem_bytes);
-cudaError_t launch_reg(const Job* d_jobs, const int* d_order, int njobs, int grid,
+// group: rows of a parity tested together by a sweep (1, 2 or 4).
+cudaError_t launch_reg(int group, const Job* d_jobs, const int* d_order, int njobs, int grid,
                        size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
+cudaError_t launch_reg_g1(const Job* d_jobs, const int* d_order, int njobs, int grid,
+                          size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
+cudaError_t launch_reg_g2(const Job* d_jobs, const int* d_order, int njobs, int grid,
+                          size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
+cudaError_t set_level_table_reg_g1(const void* tab, size_t bytes);
+cudaError_t set_level_table_reg_g2(const void* tab, size_t bytes);
 size_t tile_kernel_smem();
 int tile_count(int w, int h);
 size_t tile_gang_words(int w, int h);

@@ -1,57 +1,19 @@
-// hasf_reg.cu -- the register kernel (one CTA per image of at most 512 x 512)
-// and its launchers.
+// hasf_reg.cu -- the register kernel with four rows per sweep group, and the
+// launchers that dispatch to the instance of the chosen sweep schedule.
 #include <cstdint>
 #include <cuda_runtime.h>
 
 #include "hasf_device.cuh"
 #include "hasf_reg.cuh"
+#include "hasf_reg_kernel.cuh"
 
 namespace hasf {
 
-// Persistent CTAs of kThreads threads take register-path jobs from `order`.
-__global__ void __launch_bounds__(kThreads, 2)
-hasf_reg_kernel(const Job* __restrict__ jobs, const int* __restrict__ order, int njobs,
-                unsigned* counter) {
-  extern __shared__ uint4 smem4[];
-  uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
-  __shared__ int next;
-  for (;;) {
-    if (threadIdx.x == 0) next = (int)atomicAdd(counter, 1u);
-    __syncthreads();
-    const int slot = next;
-    __syncthreads();
-    if (slot >= njobs) break;
-    const Job& jb = jobs[order[slot]];
-    RegCtx k;
-    Ctx<SmemMode>& g = k.g;
-    g.w = jb.w;
-    g.h = jb.h;
-    g.wpr = jb.wpr;
-    g.P = row_pitch(jb.w);
-    const int rem = jb.w & 31;
-    g.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
-    g.S = nullptr;
-    g.F = smem + 1 + kRegPadR * g.P;
-    g.cand = nullptr;
-    g.cap = jb.cap;
-    if (threadIdx.x < STAT_COUNT) s_reg_stats[threadIdx.x] = 0u;  // ordered by the job's first barrier
-    k.M = smem + reg_f_words(jb.w, jb.h);
-    k.cand = k.M + kRegPlane;
-    k.top = k.cand + kRegPlane;
-    k.bot = k.top + (kThreads / 32) * kRegW;
-    k.warp = threadIdx.x >> 5;
-    k.half = (threadIdx.x >> 4) & 1;
-    k.j = threadIdx.x & 15;
-    k.s0 = (2 * k.warp + k.half) * kRegR;
-    k.jin = k.j < jb.wpr;
-    if (jb.conn == 4) reg_job<4>(k, jb, smem);
-    else reg_job<8>(k, jb, smem);
-    __syncthreads();
-  }
-}
-
 cudaError_t set_level_table_reg(const void* tab, size_t bytes) {
-  return cudaMemcpyToSymbol(c_lv, tab, bytes);
+  cudaError_t e = cudaMemcpyToSymbol(c_lv, tab, bytes);
+  if (e == cudaSuccess) e = set_level_table_reg_g2(tab, bytes);
+  if (e == cudaSuccess) e = set_level_table_reg_g1(tab, bytes);
+  return e;
 }
 
 size_t reg_kernel_smem(int w, int h) { return reg_smem_bytes(w, h); }
@@ -59,20 +21,20 @@ bool reg_kernel_ok(int w, int h, int rmax) { return reg_kernel_fits(w, h, rmax);
 
 int reg_ctas_per_sm(size_t smem_bytes) {
   int n = 0;
-  cudaFuncSetAttribute(hasf_reg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(hasf_reg_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem_bytes);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hasf_reg_kernel, kThreads, smem_bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, hasf_reg_kernel<4>, kThreads, smem_bytes);
   return n;
 }
 
-cudaError_t launch_reg(const Job* d_jobs, const int* d_order, int njobs, int grid,
+cudaError_t launch_reg(int group, const Job* d_jobs, const int* d_order, int njobs, int grid,
                        size_t smem_bytes, unsigned* d_counter, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(hasf_reg_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem_bytes);
-  if (e != cudaSuccess) return e;
-  hasf_reg_kernel<<<grid, kThreads, smem_bytes, s>>>(d_jobs, d_order, njobs, d_counter);
-  return cudaGetLastError();
+  switch (group) {
+    case 1: return launch_reg_g1(d_jobs, d_order, njobs, grid, smem_bytes, d_counter, s);
+    case 2: return launch_reg_g2(d_jobs, d_order, njobs, grid, smem_bytes, d_counter, s);
+    case 4: return reg_launch_instance<4>(d_jobs, d_order, njobs, grid, smem_bytes, d_counter, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace hasf

@@ -128,43 +128,45 @@ struct EdgeRow {
 // warp is skipped.  `pack` (bits q and 16 + q: bits 31 and 0 of
 // row q) is rebuilt for this parity's rows at the end.  Returns non-zero when
 // a pixel changed.
-template <int CONN, int SY>
+template <int CONN, int SY, int G>
 __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& pack,
                                              uint32_t Wb, uint32_t Eb, const EdgeRow& xr,
                                              uint32_t& need) {
+  static_assert(G == 1 || G == 2 || G == 4, "rows per group");
+  constexpr uint32_t gm = G == 4 ? 0x55u : (G == 2 ? 0x5u : 0x1u);  // the group's rows
   uint32_t* cr = k.cand + k.s0 * kRegPitch + k.j;
   const uint32_t emask = k.j == kRegW - 1 ? 0u : 0xFFFFFFFFu;
   uint32_t changed = 0;
   uint32_t rowchg = 0;
   uint32_t again = 0;
 #pragma unroll
-  for (int r = SY; r < kRegR; r += 8) {
-    if (!((need >> r) & 0x55u)) continue;   // rows r, r + 2, r + 4, r + 6, tested together
-    uint32_t cw[4], anyc = 0;
+  for (int r = SY; r < kRegR; r += 2 * G) {
+    if (!((need >> r) & gm)) continue;   // rows r, r + 2, ..., r + 2 (G - 1), tested together
+    uint32_t cw[G], anyc = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < G; ++i) {
       cw[i] = cr[(r + 2 * i) * kRegPitch];
       anyc |= cw[i];
     }
     if (!__any_sync(0xFFFFFFFFu, anyc != 0u)) continue;
-    uint32_t v[5], L[5], R[5];               // rows r - 1, r + 1, r + 3, r + 5, r + 7
+    uint32_t v[G + 1], L[G + 1], R[G + 1];   // rows r - 1, r + 1, ..., r + 2 G - 1
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i <= G; ++i) {
       const int q = r - 1 + 2 * i;
-      if (q < 0) {
-        v[i] = xr.v; L[i] = xr.l; R[i] = xr.r;
-      } else if (q >= kRegR) {
-        v[i] = xr.v; L[i] = xr.l; R[i] = xr.r;
+      if (q < 0 || q >= kRegR) {
+        v[i] = xr.v;
+        L[i] = xr.l;
+        R[i] = xr.r;
       } else {
         v[i] = S[q];
         L[i] = __funnelshift_l(Wb << (31 - q), v[i], 1);
         R[i] = __funnelshift_r(v[i], Eb >> (16 + q), 1);
       }
     }
-    uint32_t c[4], wl[4], res[4], c0[4];
+    uint32_t c[G], wl[G], res[G], c0[G];
     uint32_t any = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < G; ++i) {
       const int q = r + 2 * i;
       c[i] = S[q];
       wl[i] = Wb << (31 - q);
@@ -177,19 +179,19 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], ui
       // odd pixels: the right word's bit 0 after its even-column pass, one
       // shuffle per row
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < G; ++i) {
         c[i] ^= c0[i];
         const uint32_t e = __shfl_down_sync(0xFFFFFFFFu, c[i], 1, 16) & emask;
         res[i] = simple_planes<CONN>(__funnelshift_r(c[i], e, 1), R[i], v[i], L[i],
                                      __funnelshift_l(wl[i], c[i], 1), L[i + 1], v[i + 1],
                                      R[i + 1]);
       }
-      rowchg |= 0x55u << r;
+      rowchg |= gm << r;
       changed = 1u;
     }
     uint32_t any1 = 0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < G; ++i) {
       const int q = r + 2 * i;
       const uint32_t c1 = res[i] & cw[i] & 0xAAAAAAAAu;
       S[q] = c[i] ^ c1;
@@ -197,8 +199,8 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], ui
       any1 |= c1;
     }
     if (__any_sync(0xFFFFFFFFu, any1 != 0u)) {
-      rowchg |= 0x55u << r;
-      again |= 0x55u << r;
+      rowchg |= gm << r;
+      again |= gm << r;
       changed = 1u;
     }
   }
@@ -247,7 +249,7 @@ __device__ __forceinline__ EdgeRow edge_row(uint32_t v, bool jfirst, bool jlast)
 
 // Rounds at one level until a round changes nothing.  False on the cap.
 // ab_prev / be_prev: the rows across the warp boundary as last seen.
-template <int CONN>
+template <int CONN, int G>
 __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint32_t& ab_prev,
                           uint32_t& be_prev) {
   const int lane = threadIdx.x & 31;
@@ -269,7 +271,7 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint3
     uint32_t Eb = __shfl_down_sync(0xFFFFFFFFu, pack, 1, 16);
     if (jfirst) Wb = 0u;
     if (jlast) Eb = 0u;
-    uint32_t ch = reg_half<CONN, 0>(k, S, pack, Wb, Eb, edge_row(ab, jfirst, jlast), need);
+    uint32_t ch = reg_half<CONN, 0, G>(k, S, pack, Wb, Eb, edge_row(ab, jfirst, jlast), need);
     if (k.half == 0) k.top[k.warp * kRegW + k.j] = S[0];
     __syncthreads();
     // odd rows: row below the strip = first row of the strip below
@@ -283,7 +285,7 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint3
     Eb = __shfl_down_sync(0xFFFFFFFFu, pack, 1, 16);
     if (jfirst) Wb = 0u;
     if (jlast) Eb = 0u;
-    ch |= reg_half<CONN, 1>(k, S, pack, Wb, Eb, edge_row(be, jfirst, jlast), need);
+    ch |= reg_half<CONN, 1, G>(k, S, pack, Wb, Eb, edge_row(be, jfirst, jlast), need);
     if (k.half == 1) k.bot[k.warp * kRegW + k.j] = S[kRegR - 1];
     if (!__syncthreads_or(ch != 0u)) return true;
   }
@@ -298,7 +300,7 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint3
 
 // One constrained thinning (thin) or thickening at radius r; the allowed
 // points are (thin ? S : complement of S) cap pos minus neg (global planes).
-template <int CONN, bool thin>
+template <int CONN, bool thin, int G>
 __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r,
                              const uint32_t* pos, const uint32_t* neg) {
   Ctx<SmemMode>& g = k.g;
@@ -392,7 +394,7 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r,
     if (lane == 0) atomicAdd(&s_reg_stats[STAT_RING_EVALS], ring);
     if (!__syncthreads_or(newrows != 0u)) continue;
     if (threadIdx.x == 0) s_reg_stats[STAT_LEVELS] += 1;
-    if (!reg_level<CONN>(k, S, need, ab_prev, be_prev)) return false;
+    if (!reg_level<CONN, G>(k, S, need, ab_prev, be_prev)) return false;
   }
   return true;
 }
@@ -459,7 +461,7 @@ __device__ __forceinline__ OpStep op_step(const Job& jb, int st) {
   return s;
 }
 
-template <int CONN>
+template <int CONN, int G>
 __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
   Ctx<SmemMode>& g = k.g;
   uint32_t S[kRegR];
@@ -502,13 +504,13 @@ __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
   bool ok = true;
   auto hc = [&](int r) {
     snapshot_g0();
-    if (!reg_operator<CONN, true>(k, S, r, nullptr, jb.cp)) return false;
-    return reg_operator<CONN, false>(k, S, r, jb.g0, nullptr);
+    if (!reg_operator<CONN, true, G>(k, S, r, nullptr, jb.cp)) return false;
+    return reg_operator<CONN, false, G>(k, S, r, jb.g0, nullptr);
   };
   auto hf = [&](int r) {
     snapshot_g0();
-    if (!reg_operator<CONN, false>(k, S, r, nullptr, jb.dp)) return false;
-    return reg_operator<CONN, true>(k, S, r, nullptr, jb.g0);
+    if (!reg_operator<CONN, false, G>(k, S, r, nullptr, jb.dp)) return false;
+    return reg_operator<CONN, true, G>(k, S, r, nullptr, jb.g0);
   };
   switch (jb.op) {
     case OP_HASF: {
@@ -541,8 +543,8 @@ __device__ void reg_job(RegCtx& k, const Job& jb, uint32_t* smem) {
       if (ok && jb.stable && !fixed && threadIdx.x == 0) atomicMax(jb.status, (int)DEV_UNSTABLE);
       break;
     }
-    case OP_THIN: ok = reg_operator<CONN, true>(k, S, jb.r_hi, nullptr, jb.cp); break;
-    case OP_THICK: ok = reg_operator<CONN, false>(k, S, jb.r_hi, jb.cp, nullptr); break;
+    case OP_THIN: ok = reg_operator<CONN, true, G>(k, S, jb.r_hi, nullptr, jb.cp); break;
+    case OP_THICK: ok = reg_operator<CONN, false, G>(k, S, jb.r_hi, jb.cp, nullptr); break;
     case OP_HC: ok = hc(jb.r_hi); break;
     case OP_HF: ok = hf(jb.r_hi); break;
     default: ok = false;

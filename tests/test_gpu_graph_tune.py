@@ -52,16 +52,52 @@ def test_graph_replays_new_contents(ctx):
 
 
 def test_autotune_choice_and_roundtrip(ctx, tmp_path):
+    """The autotuner records a launch shape for a tiled-size bucket and a sweep
+    schedule for a register-kernel bucket; later calls use them and still equal
+    the oracle; the choices survive a save / load round trip."""
     import torch
+    from paper_1603_09337_gb300 import Context
     c = ctx.autotune(800, 640, 3)
     assert c in (-1, 0) or (c & (c - 1)) == 0    # tiled, one CTA or a power of two
-    assert ctx.autotune(400, 300, 3) == 0        # register kernel: nothing to tune
-    X = synth.shapes_image(5, 800, 640, 20, 5, 60, n_holes=3, noise_permille=50)
-    got = ctx.smooth(torch.from_numpy(X).cuda(), 3)
-    ctx.status()
-    np.testing.assert_array_equal(got.cpu().numpy(), oracle.hasf(X, 3))
+    assert ctx.tuning_get(800, 640, 3) == (c, 0)
+    assert ctx.autotune(400, 300, 3) == 0        # register kernel: its sweep schedule is tuned
+    ctas, group = ctx.tuning_get(400, 300, 3)
+    assert ctas == 0 and group in (1, 2, 4)
+    for w, h in ((800, 640), (400, 300)):
+        X = synth.shapes_image(5, w, h, 20, 5, 60, n_holes=3, noise_permille=50)
+        got = ctx.smooth(torch.from_numpy(X).cuda(), 3)
+        ctx.status()
+        np.testing.assert_array_equal(got.cpu().numpy(), oracle.hasf(X, 3))
     path = str(tmp_path / "tune.txt")
     ctx.tuning_save(path)
-    text = open(path).read().split()
-    assert text and len(text) % 4 == 0
-    ctx.tuning_load(path)
+    rows = [l.split() for l in open(path) if l.strip()]
+    assert rows and all(len(r) == 5 for r in rows)
+    with Context(0) as fresh:
+        assert fresh.tuning_get(400, 300, 3) is None
+        fresh.tuning_load(path)
+        assert fresh.tuning_get(400, 300, 3) == (0, group)
+        assert fresh.tuning_get(800, 640, 3) == (c, 0)
+
+
+@pytest.mark.parametrize("group", [1, 2, 4])
+def test_every_sweep_schedule_equals_oracle(ctx, group):
+    """The register kernel's three sweep schedules (rows of a parity tested
+    together) give the oracle's images, for both adjacencies, with C and D."""
+    import torch
+    from paper_1603_09337_gb300 import _lib
+    ctx.set_option(_lib.OPT_ROW_GROUP, group)
+    try:
+        for i, (w, h, r, conn) in enumerate([(512, 512, 5, 8), (300, 200, 3, 4), (97, 61, 2, 8),
+                                             (511, 333, 4, 4)]):
+            X = synth.shapes_image(40 + i, w, h, max(1, w * h // 20000), 5, 50, n_holes=3,
+                                   jitter=2, noise_permille=60)
+            C = synth.constraint_points(i, X, 20)
+            Dm = synth.small_random(i + 3, w, h, 20) & (1 - X)
+            t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            got = ctx.smooth(t(X), r, C=t(C), D=t(Dm), conn=conn)
+            ctx.status()
+            np.testing.assert_array_equal(got.cpu().numpy(),
+                                          oracle.hasf(X, r, C=C, D=Dm, conn=conn),
+                                          err_msg=f"{w}x{h} group {group}")
+    finally:
+        ctx.set_option(_lib.OPT_ROW_GROUP, 0)
