@@ -51,7 +51,8 @@ INT32_LANES_PER_SM = 128
 RECIPE_MIX = {"word_tests": {"shf": 6, "lop3": 14}, "ring_evals": {"shf": 1, "lop3": 1}}
 
 
-TRAFFIC_SOURCES = ("hasf_reg.cu", "hasf_reg.cuh", "hasf_device.cuh", "hasf_internal.h")
+TRAFFIC_SOURCES = ("hasf_reg.cu", "hasf_reg_kernel.cuh", "hasf_reg.cuh", "hasf_device.cuh",
+                   "hasf_internal.h")
 
 
 def _traffic_record(workload: str):

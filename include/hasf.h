@@ -183,13 +183,12 @@ int hasf_drain(hasf_ctx *ctx);
  *   HASF_OPT_WAIT_DEADLINE_MS (0..60000): how long a CTA of a gang waits at
  *                        the gang barrier for the others before the job gives
  *                        up with HASF_ETIMEOUT, 0 = 4000 ms;
- *   HASF_OPT_FAULT_GANG_SKIP (>= 0): fault injection for tests of the failure
- *                        path -- k >= 1 makes CTA 0 of every gang of two or
- *                        more CTAs leave its job at its k-th barrier without
- *                        arriving, as a CTA that died would; the others' waits
- *                        run out at the deadline and the job reports
- *                        HASF_ETIMEOUT (no device fault; the context stays
- *                        usable); 0 = off;
+ *   HASF_OPT_FAULT_GANG_SKIP (0/1): fault injection for tests of the failure
+ *                        path -- 1 makes CTA 0 of every gang of two or more
+ *                        CTAs leave its job before its first barrier, as a CTA
+ *                        that died would; the others' waits run out at the
+ *                        deadline and the job reports HASF_ETIMEOUT (no device
+ *                        fault; the context stays usable); 0 = off;
  *   HASF_OPT_FAULT_ALLOC (>= 0): fault injection -- the n-th device or pinned
  *                        host allocation the context makes from now on fails
  *                        as if the memory were exhausted (the call returns
@@ -219,8 +218,10 @@ enum {
 int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
 
 /* Work counters accumulated by launches made while HASF_OPT_STATS was 1,
- * summed over images: [0] sweep word tests (32-pixel words holding a candidate
- * of the active subfield), [1] shifted feature words read by level updates,
+ * summed over images: [0] sweep word tests (32-pixel words tested, each word
+ * counted once per subfield: the register kernel counts the rows of the groups
+ * it tests, the other kernels every word of the rows they sweep), [1] shifted
+ * feature words read by level updates,
  * [2] subfield passes, [3] priority levels that activated points, [4] rounds,
  * and [5] the number of kernel launches the context issued since the last
  * read (counted on the host whatever HASF_OPT_STATS is).  Synchronises the

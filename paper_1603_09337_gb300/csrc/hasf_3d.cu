@@ -337,9 +337,10 @@ __device__ void snapshot3(V3& v, const Job3& jb) {
 // Two CTAs per SM: the sweeps wait on gang barriers, and a second CTA hides them.
 __global__ void __launch_bounds__(kThreads, 2)
 hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
-  __shared__ int flag;
+  __shared__ __align__(8) int flag[4];  // gang barrier state (GangMode)
   const int2 m = ctamap[blockIdx.x];
   const Job3& jb = jobs[m.x];
+  if (gang_fault_leaves(jb.fault_skip, jb.gang, m.y)) return;
   V3 v;
   v.w = jb.w;
   v.h = jb.h;
@@ -349,7 +350,7 @@ hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
   v.gtid = m.y * blockDim.x + threadIdx.x;
   v.gthreads = jb.gang * blockDim.x;
   v.solo = jb.gang == 1;
-  v.gm.init(jb.sync, jb.gang, &flag, jb.deadline_ms, jb.fault_skip, m.y);
+  v.gm.init(jb.sync, jb.gang, flag, jb.deadline_ms);
   const int rem = jb.w & 31;
   v.lastmask = rem ? ((1u << rem) - 1u) : 0xFFFFFFFFu;
   v.n_tests = v.n_ring = v.n_rounds = v.n_levels = 0;

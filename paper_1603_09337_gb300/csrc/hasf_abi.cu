@@ -88,7 +88,7 @@ struct Options {
   int generic_only = 0;
   int host_mapped = 1;  // hasf_smooth_host: mapped pinned buffers used in place
   int wait_deadline_ms = 0;  // gang barrier wait limit, 0 = 4000 ms
-  int fault_gang_skip = 0;   // fault injection: CTA 0 of a gang stops at its k-th barrier
+  int fault_gang_skip = 0;   // fault injection: CTA 0 of a gang leaves before its first barrier
   int row_group = 0;         // register kernel's rows per sweep group: 0 = tuned / 4, or 1, 2, 4
 };
 
@@ -939,7 +939,7 @@ int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
       ctx->opt.wait_deadline_ms = (int)value;
       return HASF_OK;
     case HASF_OPT_FAULT_GANG_SKIP:
-      if (value < 0 || value > INT_MAX) return HASF_EINVAL;
+      if (value != 0 && value != 1) return HASF_EINVAL;
       ctx->opt.fault_gang_skip = (int)value;
       return HASF_OK;
     case HASF_OPT_FAULT_ALLOC:

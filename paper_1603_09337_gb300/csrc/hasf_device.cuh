@@ -85,43 +85,36 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // No CTA can arrive on a counter again before every CTA has left the barrier
 // that used it, so the value a CTA reads after the wait is that barrier's
 // final value.  Every wait is bounded by a deadline (4 s unless the job sets
-// another); a CTA that gives up marks the gang failed and leaves the job, and
-// a failed CTA meets no further barrier.  For tests of that path, a job can
-// ask CTA 0 of the gang to stop arriving at its k-th barrier: the others'
-// waits then run out and the job reports DEV_TIMEOUT, with no fault.
+// another); a CTA that gives up marks the gang failed and leaves the job.
 struct GangMode {
   unsigned* sync_words;
   int nctas;
-  int* flag_smem;  // shared int: broadcast of the barrier result
+  // shared, 8-byte aligned: [0] broadcast of the barrier result, [2..3] the
+  // wait limit in ns (thread 0 reads it only while it waits)
+  int* flag_smem;
   int dead;
   unsigned epoch;        // barriers passed (thread 0's copy is the one used)
   unsigned hi0, hi1;     // high half after the last barrier on each counter
-  unsigned long long deadline_ns;
-  unsigned stop_at;      // 0, or the barrier (1-based) at which this CTA stops arriving
 
   static __device__ __forceinline__ uint32_t ld(const uint32_t* p) { return __ldcg(p); }
   static __device__ __forceinline__ void st(uint32_t* p, uint32_t v) { __stcg(p, v); }
   static __device__ __forceinline__ void atomic_or(uint32_t* p, uint32_t v) { atomicOr(p, v); }
 
-  __device__ __forceinline__ void init(unsigned* words, int n, int* flag, int deadline_ms,
-                                       int fault_skip, int rank) {
+  __device__ __forceinline__ void init(unsigned* words, int n, int* flag, int deadline_ms) {
     sync_words = words;
     nctas = n;
     flag_smem = flag;
     dead = 0;
     epoch = 0;
     hi0 = hi1 = 0;
-    deadline_ns = (unsigned long long)(deadline_ms > 0 ? deadline_ms : 4000) * 1000000ull;
-    stop_at = (fault_skip > 0 && rank == 0 && n > 1) ? (unsigned)fault_skip : 0u;
+    if (threadIdx.x == 0)
+      *reinterpret_cast<unsigned long long*>(flag + 2) =
+          (unsigned long long)(deadline_ms > 0 ? deadline_ms : 4000) * 1000000ull;
   }
 
   __device__ int barrier(int v) {
-    if (dead) return 0;  // the CTA has left the job (every thread holds the same flag)
     const int any = __syncthreads_or(v);
-    if (threadIdx.x == 0 && epoch + 1u == stop_at) {
-      *flag_smem = -1;  // injected: this CTA stops arriving; the others' waits run out
-      ++epoch;
-    } else if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
       const unsigned par = epoch & 1u;
       unsigned long long* ctr = reinterpret_cast<unsigned long long*>(sync_words + 4) + par;
       const unsigned target = (epoch / 2u + 1u) * (unsigned)nctas;
@@ -136,7 +129,11 @@ struct GangMode {
           __nanosleep(32);
           c = *(volatile unsigned long long*)ctr;
           if ((unsigned)c >= target) break;
-          if ((++spins & 255u) == 0u && global_ns() - t0 > deadline_ns) { res = 0; break; }
+          if ((++spins & 255u) == 0u &&
+              global_ns() - t0 > *reinterpret_cast<const unsigned long long*>(flag_smem + 2)) {
+            res = 0;
+            break;
+          }
         } while (true);
       }
       __threadfence();
@@ -156,6 +153,15 @@ struct GangMode {
   __device__ __forceinline__ int sync_or(int v) { return barrier(v); }
   __device__ __forceinline__ bool failed() const { return dead != 0; }
 };
+
+// Fault injection for tests of the failure path: with the job's fault option
+// set, CTA 0 of a gang of two or more leaves its job before its first barrier,
+// as a CTA that died would; it still counts itself done, so that a served
+// job is reported.  The others' bounded waits run out and the job reports
+// DEV_TIMEOUT, with no device fault.
+__device__ __forceinline__ bool gang_fault_leaves(int fault_skip, int gang, int rank) {
+  return fault_skip > 0 && gang > 1 && rank == 0;
+}
 
 // ---------------------------------------------------------------------------
 // Per-job context.

@@ -23,7 +23,7 @@ enum Op : int {
 
 // Work counters a job adds to when Job::stats is set.
 enum StatIndex : int {
-  STAT_WORD_TESTS = 0,  // sweep words holding a candidate of the active subfield
+  STAT_WORD_TESTS = 0,  // sweep words tested, once per subfield
   STAT_RING_EVALS = 1,  // shifted feature words read by level updates
   STAT_PASSES = 2,      // subfield passes
   STAT_LEVELS = 3,      // levels that activated points
@@ -61,7 +61,7 @@ struct Job {
   int plane_words;   // words per padded plane (see plane_words())
   int stable;        // 1: stop after the first step r that changes nothing
   int deadline_ms;   // gang barrier wait limit (0 = 4000 ms)
-  int fault_skip;    // fault injection: k >= 1 makes CTA 0 of a gang stop at its k-th barrier
+  int fault_skip;    // fault injection: 1 makes CTA 0 of a gang leave before its first barrier
 };
 
 // One volume job of the 3D filter.  Planes: d * h rows of wpr words, bit b of
@@ -87,7 +87,7 @@ struct Job3 {
   int cap;             // rounds allowed per level
   int deadline_ms;     // gang barrier wait limit (0 = 4000 ms)
   int fault_skip;      // fault injection, as in Job
-  int pad_;
+  int pad_[3];         // 160 bytes: descriptors stay 16-byte aligned in the array
 };
 
 // Padded plane geometry shared by both modes: rows -1..h, P words per row

@@ -35,11 +35,15 @@ hasf_resident_kernel(const Job* __restrict__ jobs, const int* __restrict__ order
 // Gang mode: CTA b works on job ctamap[b].x as part ctamap[b].y of jobs[].gang.
 __global__ void __launch_bounds__(kThreads, 1)
 hasf_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) {
-  __shared__ int flag;
+  __shared__ __align__(8) int flag[4];  // gang barrier state (GangMode)
   const int2 m = ctamap[blockIdx.x];
   const Job& jb = jobs[m.x];
+  if (gang_fault_leaves(jb.fault_skip, jb.gang, m.y)) {
+    job_done(jb, jb.gang);
+    return;
+  }
   Ctx<GangMode> k;
-  k.m.init(jb.sync, jb.gang, &flag, jb.deadline_ms, jb.fault_skip, m.y);
+  k.m.init(jb.sync, jb.gang, flag, jb.deadline_ms);
   init_ctx(k, jb, jb.planes, m.y * blockDim.x + threadIdx.x, jb.gang * blockDim.x);
   if (jb.conn == 4) run_job<GangMode, 4>(k, jb, jb.planes);
   else run_job<GangMode, 8>(k, jb, jb.planes);

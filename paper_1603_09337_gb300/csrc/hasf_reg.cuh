@@ -149,6 +149,8 @@ __device__ __forceinline__ uint32_t reg_half(RegCtx& k, uint32_t (&S)[kRegR], ui
       anyc |= cw[i];
     }
     if (!__any_sync(0xFFFFFFFFu, anyc != 0u)) continue;
+    // work counter: the group's rows, both subfields, every lane
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_reg_stats[STAT_WORD_TESTS], 64u * G);
     uint32_t v[G + 1], L[G + 1], R[G + 1];   // rows r - 1, r + 1, ..., r + 2 G - 1
 #pragma unroll
     for (int i = 0; i <= G; ++i) {
@@ -266,7 +268,6 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint3
     if (k.half == 0) ab = k.warp > 0 ? k.bot[(k.warp - 1) * kRegW + k.j] : 0u;
     if (__any_sync(0xFFFFFFFFu, ab != ab_prev)) need |= 1u;
     ab_prev = ab;
-    if (lane == 0) atomicAdd(&s_reg_stats[STAT_WORD_TESTS], 64u * __popc(need & 0x5555u));
     uint32_t Wb = __shfl_up_sync(0xFFFFFFFFu, pack, 1, 16);
     uint32_t Eb = __shfl_down_sync(0xFFFFFFFFu, pack, 1, 16);
     if (jfirst) Wb = 0u;
@@ -280,7 +281,6 @@ __device__ bool reg_level(RegCtx& k, uint32_t (&S)[kRegR], uint32_t& need, uint3
       be = (k.warp + 1) < (int)(blockDim.x >> 5) ? k.top[(k.warp + 1) * kRegW + k.j] : 0u;
     if (__any_sync(0xFFFFFFFFu, be != be_prev)) need |= 0x8000u;
     be_prev = be;
-    if (lane == 0) atomicAdd(&s_reg_stats[STAT_WORD_TESTS], 64u * __popc(need & 0xAAAAu));
     Wb = __shfl_up_sync(0xFFFFFFFFu, pack, 1, 16);
     Eb = __shfl_down_sync(0xFFFFFFFFu, pack, 1, 16);
     if (jfirst) Wb = 0u;

@@ -49,14 +49,18 @@ __global__ void __launch_bounds__(kThreads, MINB)
 hasf_tile_gang_kernel(const Job* __restrict__ jobs, const int2* __restrict__ ctamap) {
   extern __shared__ uint4 smem4[];
   uint32_t* smem = reinterpret_cast<uint32_t*>(smem4);
-  __shared__ int flag;
+  __shared__ __align__(8) int flag[4];  // gang barrier state (GangMode)
   const int2 m = ctamap[blockIdx.x];
   const Job& jb = jobs[m.x];
+  if (gang_fault_leaves(jb.fault_skip, jb.gang, m.y)) {
+    job_done(jb, jb.gang);
+    return;
+  }
   const int ntx = tiles_x(jb.w);
   TileCtx<GangX> k;
   tile_init(k, jb, smem, m.y % ntx, m.y / ntx);
   k.x.gbase = jb.planes;
-  k.x.gm.init(jb.sync, jb.gang, &flag, jb.deadline_ms, jb.fault_skip, m.y);
+  k.x.gm.init(jb.sync, jb.gang, flag, jb.deadline_ms);
   for (int t = threadIdx.x; t < kTileSmemWords; t += blockDim.x) smem[t] = 0u;
   __syncthreads();
   if (jb.conn == 4) tile_job<4>(k, jb, smem);

@@ -2,8 +2,8 @@
 
 A gang of CTAs (one large image, or a volume) meets at a global-memory
 barrier whose waits are bounded by a deadline.  The host-set fault option
-makes CTA 0 of every gang leave its job at its k-th barrier without arriving,
-as a CTA that died would: the other CTAs' waits run out at a short deadline,
+makes CTA 0 of every gang leave its job before its first barrier, as a CTA
+that died would: the other CTAs' waits run out at a short deadline,
 the job reports HASF_ETIMEOUT through the status word, and the context keeps
 working.  Allocation failures are injected on the host and must surface as
 HASF_ENOMEM from the call that needed the memory, with the context usable
@@ -40,8 +40,8 @@ def _expect_timeout(ctx, t0, limit_s):
 
 
 def test_gang_barrier_deadline_without_a_fault(torch_cuda):
-    """Generic gang (planes in L2) and tiled gang: CTA 0 stops arriving at its
-    third barrier, the others give up after 200 ms, the job reports
+    """Generic gang (planes in L2) and tiled gang: CTA 0 never arrives, the
+    others give up after 200 ms, the job reports
     HASF_ETIMEOUT; then the same context smooths the image correctly."""
     torch = torch_cuda
     from paper_1603_09337_gb300 import Context
@@ -58,7 +58,7 @@ def test_gang_barrier_deadline_without_a_fault(torch_cuda):
             for o, v in opts:
                 ctx.set_option(o, v)
             t = torch.from_numpy(img).cuda()
-            ctx.set_option(_lib.OPT_FAULT_GANG_SKIP, 3)
+            ctx.set_option(_lib.OPT_FAULT_GANG_SKIP, 1)
             t0 = time.perf_counter()
             ctx.smooth(t, 2)
             _expect_timeout(ctx, t0, 10.0)
@@ -77,7 +77,7 @@ def test_volume_gang_deadline_without_a_fault(torch_cuda):
     X = synth.volume(31, 64, 64, 64, 20, 3, 9, 30)
     with Context(0) as ctx:
         ctx.set_option(_lib.OPT_WAIT_DEADLINE_MS, 200)
-        ctx.set_option(_lib.OPT_FAULT_GANG_SKIP, 2)
+        ctx.set_option(_lib.OPT_FAULT_GANG_SKIP, 1)
         t = torch.from_numpy(X).cuda()
         t0 = time.perf_counter()
         ctx.smooth3d([(t, 2, None, None)])
@@ -130,7 +130,8 @@ def test_fault_options_are_checked(torch_cuda):
     from paper_1603_09337_gb300 import Context
     with Context(0) as ctx:
         for opt, bad in ((_lib.OPT_WAIT_DEADLINE_MS, -1), (_lib.OPT_WAIT_DEADLINE_MS, 60001),
-                         (_lib.OPT_FAULT_GANG_SKIP, -1), (_lib.OPT_FAULT_ALLOC, -1)):
+                         (_lib.OPT_FAULT_GANG_SKIP, -1), (_lib.OPT_FAULT_GANG_SKIP, 2),
+                         (_lib.OPT_FAULT_ALLOC, -1)):
             with pytest.raises(_lib.HasfError) as e:
                 ctx.set_option(opt, bad)
             assert e.value.code == _lib.HASF_EINVAL
