@@ -126,13 +126,17 @@ int hasf_smooth_batch(hasf_ctx *ctx, const hasf_image *imgs, int n, void *stream
 int hasf_status_of(hasf_ctx *ctx, void *stream);
 
 /* Host-buffer form: every pointer in `imgs` is a HOST pointer (ordinary or
- * pinned memory).  Images whose buffers are all page-locked and mapped into
- * the device's address space (cudaHostAlloc, or cudaHostRegister with the
- * mapped flag) are gathered into device buffers by one launch of the
- * library's copy kernel (reading across the host link) and scattered back by
- * another; the others are staged through the context's pinned buffer with one
- * copy per buffer.  Synchronous: the results are in the callers' buffers on
- * return.
+ * pinned memory).  By default (HASF_OPT_HOST_MAPPED 2) the kernels read their
+ * inputs from and write their results to the callers' buffers themselves,
+ * across the host link, with no staging copies: every buffer when the device
+ * can access all host memory through the host's page tables (as on GB300 with
+ * NVLink-C2C: cudaDevAttrPageableMemoryAccess), else the buffers that are
+ * page-locked and mapped into the device's address space (cudaHostAlloc, or
+ * cudaHostRegister with the mapped flag).  HASF_OPT_HOST_MAPPED 1 moves mapped
+ * buffers with one launch of the library's copy kernel per direction instead.
+ * Other buffers are staged through the context's pinned buffer with one copy
+ * per buffer.  Synchronous: the results are in the callers' buffers on
+ * return.  The buffers must not be freed or changed during the call.
  * Errors as hasf_smooth_batch, plus HASF_ETIMEOUT. */
 int hasf_smooth_host(hasf_ctx *ctx, const hasf_image *imgs, int n);
 
@@ -176,10 +180,11 @@ int hasf_drain(hasf_ctx *ctx);
  *                        thread-block clusters when they have at most 16 tiles
  *                        of 512 x 512, else as a gang; 2: always as a gang;
  *                        0: never (generic kernels);
- *   HASF_OPT_HOST_MAPPED (0/1): hasf_smooth_host moves page-locked,
- *                        device-mapped caller buffers with one launch of the
- *                        library's copy kernel per direction (1, default)
- *                        instead of one copy call per buffer (0);
+ *   HASF_OPT_HOST_MAPPED (0/1/2): how hasf_smooth_host moves host buffers
+ *                        the device can reach -- 2 (default): the kernels read
+ *                        and write them in place; 1: page-locked mapped buffers
+ *                        through one launch of the library's copy kernel per
+ *                        direction; 0: one copy call per buffer;
  *   HASF_OPT_WAIT_DEADLINE_MS (0..60000): how long a CTA of a gang waits at
  *                        the gang barrier for the others before the job gives
  *                        up with HASF_ETIMEOUT, 0 = 4000 ms;

@@ -225,12 +225,14 @@ class Context:
         check(self.lib.hasf_tuning_load(self.h, path.encode()), "hasf_tuning_load")
 
     # -- host-buffer entry point -----------------------------------------------
-    def smooth_host(self, jobs):
-        """jobs: list of (X numpy (h, w) uint8, rmax, C or None, D or None, conn, out
-        numpy).  The arrays of one job may be row-strided views (pixels adjacent
-        in a row) sharing one row stride, the pitch."""
+    def host_descriptors(self, jobs):
+        """Descriptor array for hasf_smooth_host over host buffers, checked once,
+        for callers that smooth new contents of the same buffers again and
+        again (see smooth_host_raw).  jobs: list of (X numpy (h, w) uint8,
+        rmax, C or None, D or None, conn, out numpy); the arrays of one job may
+        be row-strided views (pixels adjacent in a row) sharing one row stride,
+        the pitch.  The arrays must stay alive while the descriptors are used."""
         arr = (_lib.HasfImage * max(1, len(jobs)))()
-        keep = []
         for i, (X, rmax, C, D, conn, out) in enumerate(jobs):
             h, w = X.shape
             pitch = X.strides[0]
@@ -239,12 +241,19 @@ class Context:
                     if (a.dtype.itemsize != 1 or a.shape != (h, w) or a.strides[1] != 1
                             or a.strides[0] != pitch):
                         raise ValueError("host images: (h, w) uint8, one row stride per job")
-                    keep.append(a)
             arr[i] = _lib.HasfImage(X.ctypes.data, out.ctypes.data,
                                     C.ctypes.data if C is not None else None,
                                     D.ctypes.data if D is not None else None,
                                     w, h, pitch, rmax, conn, 0)
-        check(self.lib.hasf_smooth_host(self.h, arr, len(jobs)), "hasf_smooth_host")
+        return arr
+
+    def smooth_host_raw(self, arr, n: int):
+        """hasf_smooth_host over a descriptor array from host_descriptors."""
+        check(self.lib.hasf_smooth_host(self.h, arr, n), "hasf_smooth_host")
+
+    def smooth_host(self, jobs):
+        """HASF of host buffers (see host_descriptors for `jobs`); synchronous."""
+        self.smooth_host_raw(self.host_descriptors(jobs), len(jobs))
 
     # -- serving ------------------------------------------------------------------
     def smooth3d(self, volumes, stream=None):

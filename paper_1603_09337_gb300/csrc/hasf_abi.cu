@@ -86,7 +86,7 @@ struct Options {
   int serve_batch = 512;
   int stats = 0;
   int generic_only = 0;
-  int host_mapped = 1;  // hasf_smooth_host: mapped pinned buffers used in place
+  int host_mapped = 2;  // hasf_smooth_host: 2 direct access, 1 copy kernel, 0 staged copies
   int wait_deadline_ms = 0;  // gang barrier wait limit, 0 = 4000 ms
   int fault_gang_skip = 0;   // fault injection: CTA 0 of a gang leaves before its first barrier
   int row_group = 0;         // register kernel's rows per sweep group: 0 = tuned / 4, or 1, 2, 4
@@ -138,6 +138,7 @@ struct hasf_ctx {
   unsigned long long* d_stats = nullptr;  // STAT_COUNT counters
   unsigned long long launches = 0;        // kernel launches issued (host count)
   int max3d = 1;                          // co-resident CTAs of the 3D kernel
+  bool pageable_access = false;           // kernels may read and write any host memory (ATS)
 
   void* pinned = nullptr;
   size_t pinned_bytes = 0;
@@ -839,6 +840,14 @@ int hasf_create(hasf_ctx** out, int device, size_t mem_budget_bytes) {
   c->gang_max = std::max(1, max_gang_ctas(device));
   c->tile_gang_max = max_tile_gang_ctas(device);
   c->max3d = std::max(1, max_3d_ctas(device));
+  {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    c->pageable_access = v != 0;
+  }
   for (int l = 0; l < 8; ++l) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) c->lanes.push_back(st);
@@ -931,7 +940,7 @@ int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
       ctx->opt.tile_force = (int)value == 2 ? 2 : 0;
       return HASF_OK;
     case HASF_OPT_HOST_MAPPED:
-      if (value != 0 && value != 1) return HASF_EINVAL;
+      if (value < 0 || value > 2) return HASF_EINVAL;
       ctx->opt.host_mapped = (int)value;
       return HASF_OK;
     case HASF_OPT_WAIT_DEADLINE_MS:
@@ -1233,8 +1242,16 @@ int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
   if (n == 0) return HASF_OK;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_status(e);
-  // Mapped page-locked images move through the copy kernel; the rest are
-  // staged through the context's pinned buffer with one copy per buffer.
+  // Direct access (HASF_OPT_HOST_MAPPED 2): the kernels read and write the
+  // callers' buffers themselves -- every buffer when the device reaches all
+  // host memory through the host's page tables, else the page-locked mapped
+  // ones (through their device addresses).  Mapped buffers can instead move
+  // through the copy kernel (1); the rest are staged through the context's
+  // pinned buffer with one copy per buffer.
+  if (ctx->opt.host_mapped == 2 && ctx->pageable_access) {
+    int rc = run_images(ctx, imgs, n, OP_HASF, ctx->host_stream);
+    return rc == HASF_OK ? hasf_status_of(ctx, ctx->host_stream) : rc;
+  }
   std::vector<hasf_image> mapped, staged;
   for (int i = 0; i < n; ++i) {
     hasf_image m;
@@ -1242,7 +1259,13 @@ int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
     else staged.push_back(imgs[i]);
   }
   if (!mapped.empty()) {
-    int rc = smooth_host_mapped(ctx, mapped.data(), (int)mapped.size());
+    int rc;
+    if (ctx->opt.host_mapped == 2) {
+      rc = run_images(ctx, mapped.data(), (int)mapped.size(), OP_HASF, ctx->host_stream);
+      if (rc == HASF_OK) rc = hasf_status_of(ctx, ctx->host_stream);
+    } else {
+      rc = smooth_host_mapped(ctx, mapped.data(), (int)mapped.size());
+    }
     if (rc) return rc;
   }
   return staged.empty() ? HASF_OK : smooth_host_staged(ctx, staged.data(), (int)staged.size());

@@ -251,12 +251,13 @@ def test_host_buffers(ctx):
 
 
 def test_host_buffers_pinned_mapped_and_staged(ctx):
-    """Pinned host buffers, some with padded rows, one job pageable: moved by
+    """Pinned host buffers, some with padded rows, one job pageable: read and
+    written by the kernels in place (direct access, the default), moved by
     the library's copy kernel over the mapping, or by one copy per buffer;
     the results equal the oracle and the row padding is left untouched."""
     import torch
     jobs = _mixed_jobs()[:6]
-    for mapped in (1, 0):
+    for mapped in (2, 1, 0):
         ctx.set_option(_lib.OPT_HOST_MAPPED, mapped)
         specs, pads = [], []
         for k, (X, r, C, cn) in enumerate(jobs):
@@ -278,22 +279,23 @@ def test_host_buffers_pinned_mapped_and_staged(ctx):
             w = X.shape[1]
             np.testing.assert_array_equal(bo[:, :w], oracle.hasf(X, r, C=C, conn=cn))
             assert (bo[:, w:] == 7).all()
-    ctx.set_option(_lib.OPT_HOST_MAPPED, 1)
-    # rows of whole 16-byte chunks: the copy kernel's vector path
-    wide = [case_image(400 + i, 96 + 64 * i, 512 - 128 * i) for i in range(3)]
-    hw = [torch.from_numpy(x).pin_memory().numpy() for x in wide]
-    hwo = [torch.from_numpy(np.zeros_like(x)).pin_memory().numpy() for x in wide]
-    ctx.smooth_host([(x, 2, None, None, 8, o) for x, o in zip(hw, hwo)])
-    for x, o in zip(wide, hwo):
-        np.testing.assert_array_equal(o, oracle.hasf(x, 2))
-    # forty pinned images in one call
-    xs = [case_image(300 + i, 40 + i, 70 - i) for i in range(40)]
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
-    hx = [pin(x) for x in xs]
-    ho = [pin(np.zeros_like(x)) for x in xs]
-    ctx.smooth_host([(x, 1 + i % 3, None, None, 8, o) for i, (x, o) in enumerate(zip(hx, ho))])
-    for i, (x, o) in enumerate(zip(xs, ho)):
-        np.testing.assert_array_equal(o, oracle.hasf(x, 1 + i % 3), err_msg=f"image {i}")
+    wide = [case_image(400 + i, 96 + 64 * i, 512 - 128 * i) for i in range(3)]
+    xs = [case_image(300 + i, 40 + i, 70 - i) for i in range(40)]
+    for mapped in (1, 2):
+        ctx.set_option(_lib.OPT_HOST_MAPPED, mapped)
+        # rows of whole 16-byte chunks: the copy kernel's vector path
+        hw = [pin(x) for x in wide]
+        hwo = [pin(np.zeros_like(x)) for x in wide]
+        ctx.smooth_host([(x, 2, None, None, 8, o) for x, o in zip(hw, hwo)])
+        for x, o in zip(wide, hwo):
+            np.testing.assert_array_equal(o, oracle.hasf(x, 2))
+        # forty pinned images in one call
+        hx = [pin(x) for x in xs]
+        ho = [pin(np.zeros_like(x)) for x in xs]
+        ctx.smooth_host([(x, 1 + i % 3, None, None, 8, o) for i, (x, o) in enumerate(zip(hx, ho))])
+        for i, (x, o) in enumerate(zip(xs, ho)):
+            np.testing.assert_array_equal(o, oracle.hasf(x, 1 + i % 3), err_msg=f"image {i}")
 
 
 def test_invalid_arguments(ctx):
