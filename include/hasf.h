@@ -126,16 +126,18 @@ int hasf_smooth_batch(hasf_ctx *ctx, const hasf_image *imgs, int n, void *stream
 int hasf_status_of(hasf_ctx *ctx, void *stream);
 
 /* Host-buffer form: every pointer in `imgs` is a HOST pointer (ordinary or
- * pinned memory).  By default (HASF_OPT_HOST_MAPPED 2) the kernels read their
- * inputs from and write their results to the callers' buffers themselves,
- * across the host link, with no staging copies: every buffer when the device
- * can access all host memory through the host's page tables (as on GB300 with
- * NVLink-C2C: cudaDevAttrPageableMemoryAccess), else the buffers that are
- * page-locked and mapped into the device's address space (cudaHostAlloc, or
- * cudaHostRegister with the mapped flag).  HASF_OPT_HOST_MAPPED 1 moves mapped
- * buffers with one launch of the library's copy kernel per direction instead.
- * Other buffers are staged through the context's pinned buffer with one copy
- * per buffer.  Synchronous: the results are in the callers' buffers on
+ * pinned memory).  By default (HASF_OPT_HOST_MAPPED 2) the register kernel
+ * (images of at most 512 x 512, rmax <= 31), which reads each input byte once
+ * and writes each output byte once, reads and writes the callers' buffers
+ * itself, across the host link, with no staging copies: any buffer when the
+ * device can access all host memory through the host's page tables (as on
+ * GB300 with NVLink-C2C: cudaDevAttrPageableMemoryAccess), else the buffers
+ * that are page-locked and mapped into the device's address space
+ * (cudaHostAlloc, or cudaHostRegister with the mapped flag).  Mapped buffers
+ * of larger images (and, under HASF_OPT_HOST_MAPPED 1, all mapped buffers)
+ * move with one launch of the library's copy kernel per direction.  Other
+ * buffers are staged through the context's pinned buffer with one copy per
+ * buffer.  Synchronous: the results are in the callers' buffers on
  * return.  The buffers must not be freed or changed during the call.
  * Errors as hasf_smooth_batch, plus HASF_ETIMEOUT. */
 int hasf_smooth_host(hasf_ctx *ctx, const hasf_image *imgs, int n);
@@ -181,10 +183,11 @@ int hasf_drain(hasf_ctx *ctx);
  *                        of 512 x 512, else as a gang; 2: always as a gang;
  *                        0: never (generic kernels);
  *   HASF_OPT_HOST_MAPPED (0/1/2): how hasf_smooth_host moves host buffers
- *                        the device can reach -- 2 (default): the kernels read
- *                        and write them in place; 1: page-locked mapped buffers
- *                        through one launch of the library's copy kernel per
- *                        direction; 0: one copy call per buffer;
+ *                        the device can reach -- 2 (default): the register
+ *                        kernel's images in place, the others as in 1;
+ *                        1: page-locked mapped buffers through one launch of
+ *                        the library's copy kernel per direction; 0: one copy
+ *                        call per buffer;
  *   HASF_OPT_WAIT_DEADLINE_MS (0..60000): how long a CTA of a gang waits at
  *                        the gang barrier for the others before the job gives
  *                        up with HASF_ETIMEOUT, 0 = 4000 ms;
@@ -356,10 +359,13 @@ int hasf_levels(hasf_ctx *ctx, const uint8_t *feat, int32_t width, int32_t heigh
  * stall on cudaMalloc (which can synchronise the device), and code inside a
  * host framework or plug-in whose device memory belongs to that framework's
  * allocator.  It smooths one image like hasf_smooth, asynchronously on
- * `stream`, with no context: the kernel's scratch (an input snapshot and the
- * packed C and D planes) lives in a fixed array inside the library (about
- * 240 KB, held on every GPU that loads the library until the process exits).
- * It calls no cudaMalloc, cudaFree or other allocating routine.
+ * `stream`, with no context, in one launch of one CTA: the register kernel of
+ * hasf_smooth for images of at most 512 x 512 with rmax <= 31, else the fused
+ * kernel with its bit planes in shared memory.  The kernels' scratch (an input
+ * snapshot and the packed C and D planes) lives in a fixed array inside the
+ * library (about 240 KB, held on every GPU that loads the library until the
+ * process exits).  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
  *
  * Limit: height * ceil(width / 32) <= 20480 and the image's three bit planes
  * must fit one CTA's shared memory (about 1130 rows at 512 columns, 560 rows at

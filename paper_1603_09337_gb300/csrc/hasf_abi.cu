@@ -1242,30 +1242,33 @@ int hasf_smooth_host(hasf_ctx* ctx, const hasf_image* imgs, int n) {
   if (n == 0) return HASF_OK;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_status(e);
-  // Direct access (HASF_OPT_HOST_MAPPED 2): the kernels read and write the
-  // callers' buffers themselves -- every buffer when the device reaches all
-  // host memory through the host's page tables, else the page-locked mapped
-  // ones (through their device addresses).  Mapped buffers can instead move
-  // through the copy kernel (1); the rest are staged through the context's
-  // pinned buffer with one copy per buffer.
-  if (ctx->opt.host_mapped == 2 && ctx->pageable_access) {
-    int rc = run_images(ctx, imgs, n, OP_HASF, ctx->host_stream);
-    return rc == HASF_OK ? hasf_status_of(ctx, ctx->host_stream) : rc;
-  }
-  std::vector<hasf_image> mapped, staged;
+  // Direct access (HASF_OPT_HOST_MAPPED 2) for the images of the register
+  // kernel, which reads every input byte once and writes every output byte
+  // once: it reads and writes the callers' buffers itself -- any buffer when
+  // the device reaches all host memory through the host's page tables, else
+  // the page-locked mapped ones (through their device addresses).  The other
+  // kernels read their inputs more than once (tile halos, reloads), so their
+  // mapped buffers move through the copy kernel (also mode 1 for all mapped
+  // buffers), and the rest are staged through the context's pinned buffer
+  // with one copy per buffer.
+  std::vector<hasf_image> direct, mapped, staged;
   for (int i = 0; i < n; ++i) {
     hasf_image m;
-    if (ctx->opt.host_mapped && mapped_image(imgs[i], m)) mapped.push_back(m);
-    else staged.push_back(imgs[i]);
+    const bool mp = ctx->opt.host_mapped && mapped_image(imgs[i], m);
+    if (ctx->opt.host_mapped == 2 && uses_reg(ctx, imgs[i]) && (ctx->pageable_access || mp))
+      direct.push_back(ctx->pageable_access ? imgs[i] : m);
+    else if (mp)
+      mapped.push_back(m);
+    else
+      staged.push_back(imgs[i]);
+  }
+  if (!direct.empty()) {
+    int rc = run_images(ctx, direct.data(), (int)direct.size(), OP_HASF, ctx->host_stream);
+    if (rc == HASF_OK) rc = hasf_status_of(ctx, ctx->host_stream);
+    if (rc) return rc;
   }
   if (!mapped.empty()) {
-    int rc;
-    if (ctx->opt.host_mapped == 2) {
-      rc = run_images(ctx, mapped.data(), (int)mapped.size(), OP_HASF, ctx->host_stream);
-      if (rc == HASF_OK) rc = hasf_status_of(ctx, ctx->host_stream);
-    } else {
-      rc = smooth_host_mapped(ctx, mapped.data(), (int)mapped.size());
-    }
+    int rc = smooth_host_mapped(ctx, mapped.data(), (int)mapped.size());
     if (rc) return rc;
   }
   return staged.empty() ? HASF_OK : smooth_host_staged(ctx, staged.data(), (int)staged.size());

@@ -131,6 +131,10 @@ cudaError_t launch_reg_g1(const Job* d_jobs, const int* d_order, int njobs, int 
                           size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
 cudaError_t launch_reg_g2(const Job* d_jobs, const int* d_order, int njobs, int grid,
                           size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
+// One image on one CTA of the register kernel, the job passed by value (no
+// device memory for a job list); reg_one_prepare once per device first.
+cudaError_t reg_one_prepare();
+cudaError_t launch_reg_one(const Job& jb, cudaStream_t s);
 cudaError_t set_level_table_reg_g1(const void* tab, size_t bytes);
 cudaError_t set_level_table_reg_g2(const void* tab, size_t bytes);
 size_t tile_kernel_smem();

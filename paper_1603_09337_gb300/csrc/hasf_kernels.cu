@@ -289,12 +289,13 @@ cudaError_t launch_levels(const uint8_t* feat, int w, int h, int pitch, int mode
 // stall on an allocation (cudaMalloc may synchronise the device), and code
 // running inside a host framework or plug-in whose device memory is owned by
 // that framework's allocator and budget.  hasf_smooth_noalloc serves them: it
-// runs one image through the same fused kernel as hasf_smooth, in resident
-// mode (one CTA, bit planes in shared memory), and keeps the kernel's global
-// scratch -- the operator-input snapshot and the packed C and D planes -- in
-// the file-scope array below instead of memory from a context.  The array is
-// part of the library image: every GPU that loads the library holds it
-// (about 240 KB) until the process exits.
+// runs one image on one CTA, through the register kernel (the job passed by
+// value) when the image is at most 512 x 512 and rmax <= 31, else through the
+// fused kernel in resident mode (bit planes in shared memory), and keeps the
+// kernels' global scratch -- the operator-input snapshot and the packed C and
+// D planes -- in the file-scope array below instead of memory from a context.
+// The array is part of the library image: every GPU that loads the library
+// holds it (about 240 KB) until the process exits.
 // ---------------------------------------------------------------------------
 namespace hasf {
 
@@ -350,6 +351,7 @@ extern "C" int hasf_smooth_noalloc(const hasf_image* img, int* status, void* str
       if (e != cudaSuccess) return HASF_ECUDA;
       e = cudaFuncSetAttribute(hasf_single_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                v - 1024);
+      if (e == cudaSuccess) e = reg_one_prepare();
       if (e != cudaSuccess) return HASF_ECUDA;
       g_noalloc_smem[dev] = (size_t)v - 1024;
       g_noalloc_ptr[dev] = (uint32_t*)p;
@@ -358,7 +360,8 @@ extern "C" int hasf_smooth_noalloc(const hasf_image* img, int* status, void* str
     smem_limit = g_noalloc_smem[dev];
   }
   const long long words = (long long)h * words_per_row(w);
-  const size_t smem = resident_smem_bytes(w, h);
+  const bool reg = reg_kernel_ok(w, h, img->rmax);
+  const size_t smem = reg ? reg_kernel_smem(w, h) : resident_smem_bytes(w, h);
   if (words > kStaticPlaneWords || smem > smem_limit) return HASF_EBUDGET;
 
   Job jb{};
@@ -386,7 +389,11 @@ extern "C" int hasf_smooth_noalloc(const hasf_image* img, int* status, void* str
   // kernel before they are read.
   e = cudaMemsetAsync(jb.status, 0, sizeof(int), s);
   if (e != cudaSuccess) return HASF_ECUDA;
-  hasf_single_kernel<<<1, kThreads, smem, s>>>(jb);
-  e = cudaGetLastError();
+  if (reg) {
+    e = launch_reg_one(jb, s);
+  } else {
+    hasf_single_kernel<<<1, kThreads, smem, s>>>(jb);
+    e = cudaGetLastError();
+  }
   return e == cudaSuccess ? HASF_OK : HASF_ECUDA;
 }

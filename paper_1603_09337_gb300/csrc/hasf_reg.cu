@@ -27,6 +27,17 @@ int reg_ctas_per_sm(size_t smem_bytes) {
   return n;
 }
 
+// The one-job kernel (four rows per sweep group): its shared-memory limit is
+// raised once to what the largest register-path image needs.
+cudaError_t reg_one_prepare() {
+  return cudaFuncSetAttribute(hasf_reg_one_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)reg_smem_bytes(32 * kRegW, kRegRows));
+}
+cudaError_t launch_reg_one(const Job& jb, cudaStream_t s) {
+  hasf_reg_one_kernel<4><<<1, kThreads, reg_smem_bytes(jb.w, jb.h), s>>>(jb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_reg(int group, const Job* d_jobs, const int* d_order, int njobs, int grid,
                        size_t smem_bytes, unsigned* d_counter, cudaStream_t s) {
   switch (group) {

@@ -77,15 +77,27 @@ def test_noalloc_equals_hasf_smooth_on_two_calls(env):
 
 
 def test_noalloc_ragged_and_near_limit_equal_oracle(env):
-    """Widths that are not a multiple of 32 (a partial last word), a row pitch
-    above the width, C and D together, (4,8) adjacency, and an image near the
-    shared-memory bound of the entry point (500 x 1130): equal to the oracle
-    and to hasf_smooth, and the bytes past the width are left untouched."""
+    """Both kernels of the entry point -- the register kernel (images up to
+    512 x 512, rmax <= 31) and the fused shared-memory kernel (larger images,
+    larger rmax) -- on widths that are not a multiple of 32 (a partial last
+    word), a row pitch above the width, C and D together, (4,8) adjacency, and
+    an image near the shared-memory bound of the entry point (500 x 1130):
+    equal to the oracle and to hasf_smooth, and the bytes past the width are
+    left untouched."""
     import torch
     ctx, lib = env
     stream = torch.cuda.current_stream()
     status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
     cases = []
+    # register kernel: 300 x 317 with C and D, (4,8); 509 x 511 at its rmax bound
+    X = synth.shapes_image(4141, 300, 317, 4, 8, 50, n_holes=2, jitter=2, noise_permille=40)
+    cases.append((X, synth.constraint_points(5, X, 15),
+                  synth.small_random(6, 300, 317, 30) & (1 - X), 3, 4, 352))
+    X = synth.shapes_image(4040, 509, 511, 3, 20, 120, n_holes=3, jitter=2, noise_permille=20)
+    cases.append((X, None, None, 31, 8, 512))
+    # fused kernel: rmax above the register kernel's bound; width above 512
+    X = synth.shapes_image(3939, 150, 200, 3, 10, 40, n_holes=2, jitter=2, noise_permille=30)
+    cases.append((X, None, None, 33, 8, 208))
     X = synth.shapes_image(4242, 517, 300, 3, 10, 60, n_holes=2, jitter=2, noise_permille=40)
     C = synth.constraint_points(7, X, 20)
     Dm = synth.small_random(8, 517, 300, 30) & (1 - X)
