@@ -40,10 +40,11 @@ WORKLOAD = ("batch of 256 synthetic 512x512 binary images (discs/ellipses, holes
 # neighbours, 8 logic operations for the four crossing terms, 4 to count
 # exactly one, 2 to gate by the candidates and update the set; one ring read
 # of a level update = 1 funnel shift + 1 OR.
-# 3D: one voxel test = 27 lane-ops to assemble the 27-bit neighbourhood plus
-# at least two dilation steps of each of the two flood fills (about 18 each),
-# counted as 100; one ring read of a word = funnel shift + AND/OR + address, 4.
-OPS_PER_VOXEL_TEST = 100
+# 3D: one voxel test = 27 lane-ops to assemble the 27-bit neighbourhood, then
+# either the table read (index, shift, mask: 5) or at least two dilation steps
+# of each of the two flood fills (about 18 each), counted as 100; one ring read
+# of a word = funnel shift + AND/OR + address, 4.
+OPS_PER_VOXEL_TEST = {"table": 32, "flood fill": 100}
 OPS_PER_RING3_EVAL = 4
 INT32_LANES_PER_SM = 128
 # Lane-operations of the recipe by instruction class: per word test 6 funnel
@@ -442,6 +443,8 @@ def run_volume(args):
     dev = torch.device("cuda", local)
     build.build()
     ctx = Context(local)
+    simple_test = "flood fill" if args.simple3_flood else "table"
+    ctx.set_option(_lib.OPT_SIMPLE3_TABLE, 0 if args.simple3_flood else 1)
     n = 16
     jobs = synth.volume_batch(n, 128, first=rank * n)
     Xs = [torch.from_numpy(j.X).to(dev) for j in jobs]
@@ -505,7 +508,8 @@ def run_volume(args):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = sms * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12
-    ops = stats["word_tests"] * OPS_PER_VOXEL_TEST + stats["ring_evals"] * OPS_PER_RING3_EVAL
+    ops = (stats["word_tests"] * OPS_PER_VOXEL_TEST[simple_test]
+           + stats["ring_evals"] * OPS_PER_RING3_EVAL)
     achieved = ops / (ms_per_step / 1e3) / 1e12
     vox = sum(x.numel() for x in Xs)
     cpu = None
@@ -524,6 +528,7 @@ def run_volume(args):
         "config": {"workload": "batch of 16 synthetic 128^3 volumes (balls of radius 4-16, "
                                "3% noise), rmax=4, (26,6) adjacency, one hasf_smooth3d call",
                    "volumes_per_step": n, "mvoxel_per_s": vox * args.steps * ws / (t_ms / 1e3) / 1e6,
+                   "simple_voxel_test": simple_test,
                    "l2": "flushed between timed steps (256 MB write, untimed)", "wall_s": wall},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                      "frac": achieved / alu_peak, "traffic": None,
@@ -803,6 +808,8 @@ def main():
                     help="skip the one-launch-per-image comparison")
     ap.add_argument("--conn", type=int, default=8, choices=[8, 4],
                     help="adjacency of the object: 8 = (8,4), 4 = (4,8)")
+    ap.add_argument("--simple3-flood", action="store_true",
+                    help="volume workload: simple-voxel test by flood fill, not the table")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -207,6 +207,12 @@ int hasf_drain(hasf_ctx *ctx);
  *                        and one shuffle round); 0 (default) = the autotuner's
  *                        choice for the image's size bucket, else 4.  The result
  *                        is the same for every schedule.
+ *   HASF_OPT_SIMPLE3_TABLE (0/1): hasf_smooth3d's simple-voxel test -- 1
+ *                        (default): one read of a table of all 2^26
+ *                        neighbourhoods (8 MB of device memory, built by the
+ *                        context's first volume call from the flood-fill test
+ *                        and kept until hasf_destroy); 0: the flood fills of
+ *                        the neighbourhood in every test.  The same result.
  * Errors: HASF_EINVAL for an unknown option or value. */
 enum {
     HASF_OPT_FORCE_GANG = 1,
@@ -221,7 +227,8 @@ enum {
     HASF_OPT_WAIT_DEADLINE_MS = 10,
     HASF_OPT_FAULT_GANG_SKIP = 11,
     HASF_OPT_FAULT_ALLOC = 12,
-    HASF_OPT_ROW_GROUP = 13
+    HASF_OPT_ROW_GROUP = 13,
+    HASF_OPT_SIMPLE3_TABLE = 14
 };
 int hasf_set_option(hasf_ctx *ctx, int option, int64_t value);
 
@@ -341,6 +348,17 @@ int hasf_operator(hasf_ctx *ctx, int op, const hasf_image *img, void *stream);
  * neighbour codes (bit k = neighbour k in the order E, NE, N, NW, W, SW, S,
  * SE; y grows downward).  out256: HOST array receiving 0/1.  Synchronous. */
 int hasf_simple_table(hasf_ctx *ctx, int32_t connectivity, uint8_t *out256);
+
+/* The simple-voxel table hasf_smooth3d reads (HASF_OPT_SIMPLE3_TABLE 1), for
+ * checking it: built on `stream` if the context has none yet (waited for),
+ * then copied asynchronously on `stream` into the DEVICE array out of 2^21
+ * uint32 words.  Bit i of the table (bit i % 32 of word i / 32) is 1 when the
+ * centre voxel is simple ((26, 6) adjacency) in the 3 x 3 x 3 neighbourhood
+ * whose 26 neighbours are the bits of i: the 27-bit position code
+ * (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1) with the centre, bit 13, taken out
+ * (code bits 0..12 are bits 0..12 of i, code bits 14..26 are bits 13..25).
+ * Errors: HASF_EINVAL for a null argument, HASF_ENOMEM, HASF_ECUDA. */
+int hasf_simple3_table(hasf_ctx *ctx, uint32_t *out, void *stream);
 
 /* Priority levels as the fused kernel derives them, for checking it: for
  * every pixel of the width x height device image `feat` (pitch bytes), the

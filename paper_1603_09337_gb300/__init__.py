@@ -187,6 +187,15 @@ class Context:
               "hasf_simple_table")
         return out
 
+    def simple3_table(self, stream=None):
+        """The 3D simple-voxel table as a numpy uint32 array of 2^21 words."""
+        import torch
+        out = torch.empty(1 << 21, dtype=torch.int32, device=f"cuda:{self.device}")
+        check(self.lib.hasf_simple3_table(self.h, _ptr(out), _stream_handle(stream)),
+              "hasf_simple3_table")
+        torch.cuda.synchronize(self.device)
+        return out.cpu().numpy().view("uint32")
+
     # -- CUDA graphs and the autotuner --------------------------------------------
     def graph_create(self, images: list[Image]):
         """Capture one batched launch of `images` (buffers fixed) as a CUDA graph."""

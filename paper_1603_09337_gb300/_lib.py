@@ -27,6 +27,7 @@ OPT_WAIT_DEADLINE_MS = 10
 OPT_FAULT_GANG_SKIP = 11
 OPT_FAULT_ALLOC = 12
 OPT_ROW_GROUP = 13
+OPT_SIMPLE3_TABLE = 14
 STAT_NAMES = ("word_tests", "ring_evals", "passes", "levels", "rounds", "launches")
 
 OP_THIN, OP_THICK, OP_HC, OP_HF = 1, 2, 3, 4
@@ -36,7 +37,7 @@ EXPORTS = (
     "hasf_create", "hasf_destroy", "hasf_smooth", "hasf_smooth_batch", "hasf_status_of",
     "hasf_smooth_host", "hasf_submit", "hasf_poll", "hasf_cancel", "hasf_drain",
     "hasf_set_option", "hasf_strerror", "hasf_edt", "hasf_operator", "hasf_simple_table",
-    "hasf_levels", "hasf_read_stats", "hasf_smooth_noalloc", "hasf_graph_create",
+    "hasf_simple3_table", "hasf_levels", "hasf_read_stats", "hasf_smooth_noalloc", "hasf_graph_create",
     "hasf_graph_launch", "hasf_graph_destroy", "hasf_autotune", "hasf_tuning_save",
     "hasf_tuning_load", "hasf_tuning_get", "hasf_smooth3d",
 )
@@ -101,6 +102,7 @@ def _declare(lib):
                              ctypes.c_int32, vp, vp]
     lib.hasf_operator.argtypes = [vp, ci, img_p, vp]
     lib.hasf_simple_table.argtypes = [vp, ctypes.c_int32, vp]
+    lib.hasf_simple3_table.argtypes = [vp, vp, vp]
     lib.hasf_levels.argtypes = [vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                 ctypes.c_int32, ctypes.c_int32, vp, vp]
     lib.hasf_read_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ci]

@@ -159,8 +159,31 @@ __device__ __forceinline__ void load_window(const V3& v, const uint32_t* S, int 
   }
 }
 
-// The simple voxels among the candidate bits cw of the window's centre word.
-__device__ __forceinline__ uint32_t test_bits(V3& v, const uint64_t (&win)[9], uint32_t cw) {
+// Index of a 27-bit position code in the simple-voxel table: the 26
+// neighbour bits, the centre (bit 13) taken out.
+__device__ __forceinline__ uint32_t simple3_index(uint32_t code) {
+  return (code & 0x1FFFu) | ((code >> 14) << 13);
+}
+
+// The table, 32 codes per thread: word i holds the codes 32 i .. 32 i + 31.
+__global__ void __launch_bounds__(256) simple3_table_kernel(uint32_t* lut) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kSimple3TableWords) return;
+  uint32_t word = 0;
+  for (int b = 0; b < 32; ++b) {
+    const uint32_t idx = (i << 5) | (uint32_t)b;
+    const uint32_t code = (idx & 0x1FFFu) | ((idx >> 13) << 14);
+    if (simple3(code)) word |= 1u << b;
+  }
+  lut[i] = word;
+}
+
+// The simple voxels among the candidate bits cw of the window's centre word:
+// by the table (kTable: one read of an 8 MB table that stays in L2), else by
+// the flood fills of simple3.  The kernel is compiled once for each.
+template <bool kTable>
+__device__ __forceinline__ uint32_t test_bits(V3& v, const uint64_t (&win)[9], uint32_t cw,
+                                              const uint32_t* __restrict__ lut) {
   uint32_t chg = 0;
   while (cw) {
     const int b = __ffs(cw) - 1;
@@ -169,12 +192,20 @@ __device__ __forceinline__ uint32_t test_bits(V3& v, const uint64_t (&win)[9], u
 #pragma unroll
     for (int k = 0; k < 9; ++k) code |= (uint32_t)((win[k] >> b) & 7u) << (3 * k);
     ++v.n_tests;
-    if (simple3(code)) chg |= 1u << b;
+    bool simple;
+    if (kTable) {
+      const uint32_t idx = simple3_index(code);
+      simple = (__ldg(lut + (idx >> 5)) >> (idx & 31u)) & 1u;
+    } else {
+      simple = simple3(code);
+    }
+    if (simple) chg |= 1u << b;
   }
   return chg;
 }
 
 // One subfield (sx, sy, sz): every candidate voxel of it that is simple changes.
+template <bool kTable>
 __device__ int sweep_sub3(V3& v, const Job3& jb, bool thin, int sx, int sy, int sz) {
   const int ny = (v.h - sy + 1) >> 1, nz = (v.d - sz + 1) >> 1;
   const long long nsub = (long long)ny * nz * v.wpr;
@@ -191,7 +222,7 @@ __device__ int sweep_sub3(V3& v, const Job3& jb, bool thin, int sx, int sy, int 
     uint64_t win[9];
     load_window(v, jb.S, j, y, z, win);
     const uint32_t cur = (uint32_t)(win[4] >> 1);
-    const uint32_t chg = test_bits(v, win, cw);
+    const uint32_t chg = test_bits<kTable>(v, win, cw, jb.simple_lut);
     if (chg) {
       st_plain(jb.S + t, thin ? (cur & ~chg) : (cur | chg));
       st_plain(jb.cand + t, call & ~chg);
@@ -207,6 +238,7 @@ __device__ int sweep_sub3(V3& v, const Job3& jb, bool thin, int sx, int sy, int 
 // bit 31 sees the next word's even voxel 0 as the first subfield left it),
 // then test the odd voxels.  Only the row itself changes in these two passes,
 // and a warp's lanes load everything before any of them stores.
+template <bool kTable>
 __device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
   const int ny = (v.h - sy + 1) >> 1, nz = (v.d - sz + 1) >> 1;
   const long long nrows = (long long)ny * nz;
@@ -232,7 +264,7 @@ __device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
       const int y = sy + 2 * (int)(row % ny), z = sz + 2 * (int)(row / ny);
       load_window(v, jb.S, j, y, z, win);
       cur = (uint32_t)(win[4] >> 1);
-      ch0 = test_bits(v, win, call & 0x55555555u);
+      ch0 = test_bits<kTable>(v, win, call & 0x55555555u, jb.simple_lut);
     } else {
       cur = act ? (*(jb.S + t)) : 0u;
     }
@@ -243,7 +275,7 @@ __device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
     const uint32_t cw1 = call & 0xAAAAAAAAu;
     if (act && cw1) {
       win[4] = ((uint64_t)east << 33) | ((uint64_t)c1 << 1) | (win[4] & 1u);
-      ch1 = test_bits(v, win, cw1);
+      ch1 = test_bits<kTable>(v, win, cw1, jb.simple_lut);
     }
     __syncwarp();
     const uint32_t chg = ch0 | ch1;
@@ -258,6 +290,7 @@ __device__ int sweep_pair3(V3& v, const Job3& jb, bool thin, int sy, int sz) {
 
 // One constrained thinning (thin) or thickening of S at radius r; the points
 // allowed to change lie in pos (if given) and not in neg (if given).
+template <bool kTable>
 __device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos,
                     const uint32_t* neg) {
   for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
@@ -309,14 +342,14 @@ __device__ bool op3(V3& v, const Job3& jb, int r, bool thin, const uint32_t* pos
       int changed = 0;
       if (v.wpr <= 32) {
         for (int m = 0; m < 4; ++m) {   // (sy, sz) = (0,0), (1,0), (0,1), (1,1)
-          changed |= sweep_pair3(v, jb, thin, m & 1, m >> 1);
+          changed |= sweep_pair3<kTable>(v, jb, thin, m & 1, m >> 1);
           const int o = v.bar(m == 3 ? changed : 0);
           if (v.failed()) return false;
           if (m == 3) changed = o;
         }
       } else {
         for (int sub = 0; sub < 8; ++sub) {
-          changed |= sweep_sub3(v, jb, thin, sub & 1, (sub >> 1) & 1, sub >> 2);
+          changed |= sweep_sub3<kTable>(v, jb, thin, sub & 1, (sub >> 1) & 1, sub >> 2);
           const int o = v.bar(sub == 7 ? changed : 0);
           if (v.failed()) return false;
           if (sub == 7) changed = o;
@@ -335,6 +368,7 @@ __device__ void snapshot3(V3& v, const Job3& jb) {
 
 // CTA b works on part ctamap[b].y of job ctamap[b].x (a gang of jobs[].gang CTAs).
 // Two CTAs per SM: the sweeps wait on gang barriers, and a second CTA hides them.
+template <bool kTable>
 __global__ void __launch_bounds__(kThreads, 2)
 hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
   __shared__ __align__(8) int flag[4];  // gang barrier state (GangMode)
@@ -369,10 +403,12 @@ hasf_3d_kernel(const Job3* __restrict__ jobs, const int2* __restrict__ ctamap) {
   bool ok = !v.failed();
   for (int r = 1; ok && r <= jb.rmax; ++r) {
     snapshot3(v, jb);   // HC_r: thinning that keeps C, thickening inside its input
-    ok = op3(v, jb, r, true, nullptr, jb.cp) && op3(v, jb, r, false, jb.g0, nullptr);
+    ok = op3<kTable>(v, jb, r, true, nullptr, jb.cp) &&
+         op3<kTable>(v, jb, r, false, jb.g0, nullptr);
     if (!ok) break;
     snapshot3(v, jb);   // HF_r: thickening that avoids D, thinning that keeps its input
-    ok = op3(v, jb, r, false, nullptr, jb.dp) && op3(v, jb, r, true, nullptr, jb.g0);
+    ok = op3<kTable>(v, jb, r, false, nullptr, jb.dp) &&
+         op3<kTable>(v, jb, r, true, nullptr, jb.g0);
   }
   if (ok) {
     for (long long t = v.gtid; t < v.nw; t += v.gthreads) {
@@ -447,17 +483,26 @@ cudaError_t upload_level_table_3d() {
   return cudaMemcpyToSymbol(c_lv3, &tab, sizeof(tab));
 }
 
+cudaError_t build_simple3_table(uint32_t* lut, cudaStream_t s) {
+  simple3_table_kernel<<<(unsigned)(kSimple3TableWords / 256), 256, 0, s>>>(lut);
+  return cudaGetLastError();
+}
+
 int max_3d_ctas(int device) {
   int per_sm = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hasf_3d_kernel, kThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hasf_3d_kernel<true>, kThreads, 0);
+  int per_sm_flood = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_flood, hasf_3d_kernel<false>, kThreads, 0);
+  per_sm = std::min(per_sm, per_sm_flood);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   return per_sm * sms;
 }
 
-cudaError_t launch_3d(const Job3* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s) {
+cudaError_t launch_3d(const Job3* d_jobs, const int2* d_ctamap, int nctas, bool table,
+                      cudaStream_t s) {
   void* args[] = {(void*)&d_jobs, (void*)&d_ctamap};
-  return cudaLaunchCooperativeKernel((const void*)hasf_3d_kernel, dim3(nctas), dim3(kThreads),
-                                     args, 0, s);
+  const void* fn = table ? (const void*)hasf_3d_kernel<true> : (const void*)hasf_3d_kernel<false>;
+  return cudaLaunchCooperativeKernel(fn, dim3(nctas), dim3(kThreads), args, 0, s);
 }
 
 }  // namespace hasf

@@ -90,6 +90,7 @@ struct Options {
   int wait_deadline_ms = 0;  // gang barrier wait limit, 0 = 4000 ms
   int fault_gang_skip = 0;   // fault injection: CTA 0 of a gang leaves before its first barrier
   int row_group = 0;         // register kernel's rows per sweep group: 0 = tuned / 4, or 1, 2, 4
+  int simple3_table = 1;     // 3D simple-voxel test by the 8 MB table (1) or by flood fill (0)
 };
 
 // The server's launch resources, one per concurrent batch, made once and
@@ -133,6 +134,7 @@ struct hasf_ctx {
   Options opt;
 
   void* arena = nullptr;
+  uint32_t* simple3_lut = nullptr;  // the 3D simple-voxel table, built at the first volume call
   size_t arena_bytes = 0;
   int* d_status = nullptr;
   unsigned long long* d_stats = nullptr;  // STAT_COUNT counters
@@ -893,6 +895,7 @@ int hasf_destroy(hasf_ctx* ctx) {
   for (cudaStream_t st : ctx->lanes) cudaStreamDestroy(st);
   cudaDeviceSynchronize();
   if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->simple3_lut) cudaFree(ctx->simple3_lut);
   if (ctx->io) cudaFree(ctx->io);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -959,6 +962,10 @@ int hasf_set_option(hasf_ctx* ctx, int option, int64_t value) {
       if (value != 0 && value != 1 && value != 2 && value != 4) return HASF_EINVAL;
       ctx->opt.row_group = (int)value;
       return HASF_OK;
+    case HASF_OPT_SIMPLE3_TABLE:
+      if (value != 0 && value != 1) return HASF_EINVAL;
+      ctx->opt.simple3_table = (int)value;
+      return HASF_OK;
     default:
       return HASF_EINVAL;
   }
@@ -1007,6 +1014,36 @@ int volume_gang(const hasf_ctx* ctx, const hasf_volume& v, int nvols) {
 
 }  // namespace
 
+namespace {
+// The 3D simple-voxel table, once per context: built on stream s and waited
+// for, so that later calls on any stream find it complete.
+int ensure_simple3_table(hasf_ctx* ctx, cudaStream_t s) {
+  if (ctx->simple3_lut) return HASF_OK;
+  void* p = nullptr;
+  cudaError_t e = ctx_malloc(ctx, &p, kSimple3TableWords * 4);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = build_simple3_table((uint32_t*)p, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    return cuda_status(e);
+  }
+  ctx->simple3_lut = (uint32_t*)p;
+  return HASF_OK;
+}
+}  // namespace
+
+int hasf_simple3_table(hasf_ctx* ctx, uint32_t* out, void* stream) {
+  if (!ctx || !out) return HASF_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_status(e);
+  int rc = ensure_simple3_table(ctx, s);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(out, ctx->simple3_lut, kSimple3TableWords * 4, cudaMemcpyDeviceToDevice, s);
+  return e == cudaSuccess ? HASF_OK : cuda_status(e);
+}
+
 int hasf_smooth3d(hasf_ctx* ctx, const hasf_volume* vols, int n, void* stream) {
   if (!ctx || n < 0 || (n > 0 && !vols)) return HASF_EINVAL;
   for (int i = 0; i < n; ++i)
@@ -1015,6 +1052,11 @@ int hasf_smooth3d(hasf_ctx* ctx, const hasf_volume* vols, int n, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_status(e);
+  if (ctx->opt.simple3_table) {
+    int rc = ensure_simple3_table(ctx, s);
+    if (rc) return rc;
+  }
+  const uint32_t* lut = ctx->opt.simple3_table ? ctx->simple3_lut : nullptr;
   int first = 0;
   while (first < n) {
     // a chunk: co-resident gangs within the budget
@@ -1068,6 +1110,7 @@ int hasf_smooth3d(hasf_ctx* ctx, const hasf_volume* vols, int n, void* stream) {
       j.sync = d_sync + 8 * k;
       j.status = ctx->d_status;
       j.stats = ctx->opt.stats ? ctx->d_stats : nullptr;
+      j.simple_lut = lut;
       for (int part = 0; part < j.gang; ++part) map.push_back(make_int2(k, part));
     }
     e = cudaMemcpyAsync(base, jobs.data(), sizeof(Job3) * cnt, cudaMemcpyHostToDevice, s);
@@ -1076,7 +1119,8 @@ int hasf_smooth3d(hasf_ctx* ctx, const hasf_volume* vols, int n, void* stream) {
                           cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_sync, 0, sizeof(unsigned) * 8 * cnt, s);
     if (e == cudaSuccess)
-      e = launch_3d((const Job3*)base, (const int2*)(base + align_up(sizeof(Job3) * cnt)), ctas, s);
+      e = launch_3d((const Job3*)base, (const int2*)(base + align_up(sizeof(Job3) * cnt)), ctas,
+                    lut != nullptr, s);
     if (e != cudaSuccess) return cuda_status(e);
     ++ctx->launches;
     first += cnt;

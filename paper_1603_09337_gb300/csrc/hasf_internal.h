@@ -81,14 +81,21 @@ struct Job3 {
   unsigned* sync;      // 8 barrier words (zeroed before the launch)
   int* status;
   unsigned long long* stats;
+  const uint32_t* simple_lut;  // simple-voxel table (kSimple3TableWords), or null: flood fill
   int w, h, d, wpr;
   int rmax;
   int gang;            // CTAs of the gang
   int cap;             // rounds allowed per level
   int deadline_ms;     // gang barrier wait limit (0 = 4000 ms)
   int fault_skip;      // fault injection, as in Job
-  int pad_[3];         // 160 bytes: descriptors stay 16-byte aligned in the array
+  int pad_[1];         // 160 bytes: descriptors stay 16-byte aligned in the array
 };
+
+// The simple-voxel table of (26, 6) adjacency: bit i of the table is 1 when
+// the centre of the 3 x 3 x 3 neighbourhood with the 26 neighbour bits i (the
+// 27-bit position code with the centre bit taken out) is simple.  2^26 bits.
+constexpr size_t kSimple3TableWords = size_t(1) << 21;
+cudaError_t build_simple3_table(uint32_t* lut, cudaStream_t s);
 
 // Padded plane geometry shared by both modes: rows -1..h, P words per row
 // (P = the first odd number above the words of a row; the extra words and
@@ -117,7 +124,9 @@ cudaError_t set_level_table_tiled(const void* tab, size_t bytes);
 constexpr int kMaxR3D = 12;   // largest rmax of the 3D filter
 cudaError_t upload_level_table_3d();
 int max_3d_ctas(int device);
-cudaError_t launch_3d(const Job3* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);
+// table: every job's simple_lut is set (the table instance of the kernel).
+cudaError_t launch_3d(const Job3* d_jobs, const int2* d_ctamap, int nctas, bool table,
+                      cudaStream_t s);
 cudaError_t launch_resident(const Job* d_jobs, const int* d_order, int njobs, int grid,
                             size_t smem_bytes, unsigned* d_counter, cudaStream_t s);
 cudaError_t launch_gang(const Job* d_jobs, const int2* d_ctamap, int nctas, cudaStream_t s);

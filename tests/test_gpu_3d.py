@@ -48,8 +48,34 @@ def balls(seed, d, h, w, n, rlo, rhi, noise):
 SHAPES = [(1, 1, 1), (1, 9, 40), (5, 6, 7), (12, 13, 33), (16, 20, 64), (9, 31, 70)]
 
 
+def test_simple3_table_equals_oracle(ctx):
+    """The table the 3D kernel reads against the oracle's simple-voxel test on
+    sampled neighbourhoods: uniform, sparse and dense ones, and every code
+    whose only object neighbours are among the six face neighbours."""
+    lut = ctx.simple3_table()
+    assert lut.shape == (1 << 21,)
+    rng = np.random.default_rng(2603)
+    idx = [rng.integers(0, 1 << 26, 60000)]
+    for p in (0.1, 0.25, 0.75, 0.9):
+        bits = rng.random((30000, 26)) < p
+        idx.append((bits * (1 << np.arange(26))).sum(axis=1))
+    faces = [4, 10, 12, 14, 16, 22]             # positions of the six face neighbours
+    for m in range(64):
+        code = sum(1 << faces[k] for k in range(6) if (m >> k) & 1)
+        idx.append(np.array([(code & 0x1FFF) | ((code >> 14) << 13)]))
+    idx = np.unique(np.concatenate(idx).astype(np.int64))
+    got = (lut[idx >> 5] >> (idx & 31).astype(np.uint32)) & 1
+    codes = (idx & 0x1FFF) | ((idx >> 13) << 14)
+    want = np.array([oracle.simple3d(int(c)) for c in codes], np.uint32)
+    assert 0 < want.sum() < len(want)
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("table", [1, 0])
 @pytest.mark.parametrize("rmax", [1, 2, 3])
-def test_volumes_equal_oracle(ctx, rmax):
+def test_volumes_equal_oracle(ctx, rmax, table):
+    """Both simple-voxel tests: the table and the flood fills."""
+    ctx.set_option(_lib.OPT_SIMPLE3_TABLE, table)
     vols, want = [], []
     for i, (d, h, w) in enumerate(SHAPES):
         X = balls(100 * rmax + i, d, h, w, max(1, d * h * w // 2000), 2, 5, 0.04)
@@ -60,6 +86,7 @@ def test_volumes_equal_oracle(ctx, rmax):
         want.append(oracle.hasf3d(X, rmax, C=C, D=D))
     outs = ctx.smooth3d(vols)
     ctx.status()
+    ctx.set_option(_lib.OPT_SIMPLE3_TABLE, 1)
     for i, (o, e) in enumerate(zip(outs, want)):
         np.testing.assert_array_equal(host(o), e, err_msg=f"volume {i} {SHAPES[i]}")
 
