@@ -601,8 +601,16 @@ int run_images(hasf_ctx* ctx, const hasf_image* imgs, int n, int op, cudaStream_
     int rc = ensure_arena(ctx, need, s);
     if (rc) return rc;
     build_plan(ctx, imgs + first, cnt, op, p, (char*)ctx->arena, ctx->d_status);
-    rc = launch_plan(ctx, p, (char*)ctx->arena, s);
-    if (rc) return rc;
+    if (cnt == 1 && p.reg_split[0] == 1) {
+      // one image of the register kernel's default schedule: its descriptor
+      // goes by value in the launch, with no upload and no job counter
+      e = launch_reg_one(p.jobs[0], s);
+      if (e != cudaSuccess) return cuda_status(e);
+      ++ctx->launches;
+    } else {
+      rc = launch_plan(ctx, p, (char*)ctx->arena, s);
+      if (rc) return rc;
+    }
     first += cnt;
     if (first < n) {
       // the next chunk reuses the arena: wait for this one
@@ -832,6 +840,7 @@ int hasf_create(hasf_ctx** out, int device, size_t mem_budget_bytes) {
   if (e != cudaSuccess) return cuda_status(e);
   e = upload_level_table();
   if (e == cudaSuccess) e = upload_level_table_3d();
+  if (e == cudaSuccess) e = reg_one_prepare();
   if (e != cudaSuccess) return cuda_status(e);
   hasf_ctx* c = new (std::nothrow) hasf_ctx();
   if (!c) return HASF_ENOMEM;
