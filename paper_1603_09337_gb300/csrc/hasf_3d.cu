@@ -36,6 +36,10 @@ namespace hasf {
 
 __device__ __forceinline__ void st_plain(uint32_t* p, uint32_t v) { *p = v; }
 
+#ifndef HASF_3D_TABLE_BATCH
+#define HASF_3D_TABLE_BATCH 4
+#endif
+
 constexpr int kMaxR3 = kMaxR3D;
 constexpr int kMaxOff3 = 7300;   // lattice vectors with 0 < |v|^2 <= 144
 constexpr int kMaxLev3 = 150;
@@ -181,25 +185,51 @@ __global__ void __launch_bounds__(256) simple3_table_kernel(uint32_t* lut) {
 // The simple voxels among the candidate bits cw of the window's centre word:
 // by the table (kTable: one read of an 8 MB table that stays in L2), else by
 // the flood fills of simple3.  The kernel is compiled once for each.
+// The 27-bit position code of the voxel at bit b of the window's centre word.
+__device__ __forceinline__ uint32_t window_code(const uint64_t (&win)[9], int b) {
+  uint32_t code = 0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) code |= (uint32_t)((win[k] >> b) & 7u) << (3 * k);
+  return code;
+}
+
+// Table form: the candidates are taken kBatch at a time, their table words
+// read together, so that a lane waits for one L2 round trip per batch rather
+// than one per voxel (the voxels of one word lie in one subfield and do not
+// see each other's changes, so the order does not matter).
+constexpr int kTableBatch = HASF_3D_TABLE_BATCH;
+__device__ __forceinline__ uint32_t test_bits_table(V3& v, const uint64_t (&win)[9], uint32_t cw,
+                                                    const uint32_t* __restrict__ lut) {
+  uint32_t chg = 0;
+  while (cw) {
+    uint32_t bit[kTableBatch], idx[kTableBatch], word[kTableBatch];
+#pragma unroll
+    for (int i = 0; i < kTableBatch; ++i) {
+      bit[i] = cw & (0u - cw);   // the lowest candidate left, or 0
+      cw ^= bit[i];
+      idx[i] = simple3_index(window_code(win, bit[i] ? __ffs(bit[i]) - 1 : 0));
+    }
+#pragma unroll
+    for (int i = 0; i < kTableBatch; ++i) word[i] = bit[i] ? __ldg(lut + (idx[i] >> 5)) : 0u;
+#pragma unroll
+    for (int i = 0; i < kTableBatch; ++i) {
+      v.n_tests += bit[i] != 0u;
+      if ((word[i] >> (idx[i] & 31u)) & 1u) chg |= bit[i];
+    }
+  }
+  return chg;
+}
+
 template <bool kTable>
 __device__ __forceinline__ uint32_t test_bits(V3& v, const uint64_t (&win)[9], uint32_t cw,
                                               const uint32_t* __restrict__ lut) {
+  if (kTable) return test_bits_table(v, win, cw, lut);
   uint32_t chg = 0;
   while (cw) {
     const int b = __ffs(cw) - 1;
     cw &= cw - 1u;
-    uint32_t code = 0;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) code |= (uint32_t)((win[k] >> b) & 7u) << (3 * k);
     ++v.n_tests;
-    bool simple;
-    if (kTable) {
-      const uint32_t idx = simple3_index(code);
-      simple = (__ldg(lut + (idx >> 5)) >> (idx & 31u)) & 1u;
-    } else {
-      simple = simple3(code);
-    }
-    if (simple) chg |= 1u << b;
+    if (simple3(window_code(win, b))) chg |= 1u << b;
   }
   return chg;
 }
