@@ -116,3 +116,25 @@ def test_peak_probe_library_exports_its_symbols(lib):
     plib = ctypes.CDLL(build.PEAK_LIB)
     for name in names:
         assert hasattr(plib, name), name
+
+
+def test_host_descriptors_marshal_and_check_host_arrays():
+    """The host-buffer descriptors (built once, reused by smooth_host_raw):
+    pointers, sizes and the shared row stride of row-strided views, and a
+    clear error for arrays of one job that do not share shape and stride."""
+    import numpy as np
+    from paper_1603_09337_gb300 import Context, _lib
+    base = np.zeros((40, 64), np.uint8)
+    X, out = base[:, :50], np.zeros((40, 64), np.uint8)[:, :50]
+    C = np.zeros((40, 64), np.uint8)[:, :50]
+    arr = Context.host_descriptors(None, [(X, 3, C, None, 4, out), (X, 2, None, None, 8, out)])
+    d = arr[0]
+    assert (d.width, d.height, d.pitch, d.rmax, d.connectivity) == (50, 40, 64, 3, 4)
+    assert d.in_ == X.ctypes.data and d.out == out.ctypes.data and d.C == C.ctypes.data
+    assert not d.D and not arr[1].C
+    with pytest.raises(ValueError):
+        Context.host_descriptors(None, [(X, 3, np.zeros((40, 50), np.uint8), None, 8, out)])
+    with pytest.raises(ValueError):
+        Context.host_descriptors(None, [(X, 3, None, None, 8, np.zeros((40, 50), np.int16))])
+    assert len(Context.host_descriptors(None, [])) == 1
+    assert _lib.HasfImage is type(d)
