@@ -356,8 +356,11 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r,
       }
       if (!(pend[0] | pend[1] | pend[2] | pend[3])) continue;
       // the level's vectors, applied to the four rows at once (independent
-      // chains); stop once every pending point of the four rows is reached
+      // chains); stop once every pending point of the four rows is reached.
+      // The walk is latency-bound: unrolled eight vectors deep, with the stop
+      // checked every eight, it keeps eight vectors' reads in flight.
       const uint32_t* base = g.F + (k.s0 + g4) * g.P + k.j;
+#pragma unroll 8
       for (int o = o0; o < o1; ++o) {
         const int dx = c_lv.off[o][0], dy = c_lv.off[o][1];
         const uint32_t* p0 = base + dy * g.P + (dx >> 5);
@@ -370,7 +373,7 @@ __device__ bool reg_operator(RegCtx& k, uint32_t (&S)[kRegR], int r,
           }
         }
         ++ring;
-        if (((o - o0) & 3) == 3) {
+        if (((o - o0) & 7) == 7) {
           uint32_t left = 0;
 #pragma unroll
           for (int u = 0; u < 4; ++u) left |= pend[u] & (thin ? acc[u] : ~acc[u]);

@@ -414,6 +414,9 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r,
       }
       if (!(pend[0] | pend[1] | pend[2] | pend[3])) continue;
       const uint32_t* base = g.F + (k.s0 + g4) * kFP + k.j;
+      // unrolled eight vectors deep, the stop checked every eight (as in the
+      // register kernel's walk: latency-bound)
+#pragma unroll 8
       for (int o = o0; o < o1; ++o) {
         const int dx = c_lv.off[o][0], dy = c_lv.off[o][1];
         const uint32_t* p0 = base + dy * kFP + (dx >> 5);
@@ -426,7 +429,7 @@ __device__ bool tile_operator(TileCtx<X>& k, uint32_t (&S)[kRegR], int r,
           }
         }
         ++g.n_ring;
-        if (((o - o0) & 3) == 3) {
+        if (((o - o0) & 7) == 7) {
           uint32_t left = 0;
 #pragma unroll
           for (int u = 0; u < 4; ++u) left |= pend[u] & (thin ? acc[u] : ~acc[u]);
